@@ -25,7 +25,8 @@
  *                      activation by the selective-sending rule of Sec. III-B
  *                      (new_u < est[v]) or, optionally, the refined rule of
  *                      Sec. IV "Further Optimizations" read as the conjunction
- *                      new_u < est[v] <= old_u.
+ *                      new_u < est[v] <= old_u, decided after the update phase
+ *                      (the extra barrier that passage mentions).
  *
  * Pins: see tests/test_oracle.py (brute force over vertex subsets from Def. 1,
  * repeated min-degree deletion, closed forms, invariants, networkx).
@@ -197,6 +198,11 @@ int orc_bz(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* core)
  *   v with t < est[v] (and, when refined != 0, also est[v] <= est[u]) is
  *   recorded for activation.  After all active vertices are done, updates are
  *   written and activations applied.
+ *   The refined rule costs an extra barrier (Sec. IV, Further Optimizations):
+ *   it is decided after the updates are written, so est[v] there is v's value
+ *   after this round.  Checked against the pre-round snapshot it is wrong: v
+ *   may have lowered in the same round to a value that u's old estimate
+ *   supported.
  * Stops when no vertex is active (returns the number of rounds run) or after
  * max_rounds rounds with vertices still active (returns -1).  est_out gets
  * the estimates after the last round run.  If frontier_out is non-NULL,
@@ -238,14 +244,27 @@ int64_t orc_montresor_sync(int64_t n, const int64_t* row_ptr, const int32_t* col
             int32_t t = orc_hindex(vals, d, est[u]);
             if (t < est[u]) {
                 upd_id[nupd] = u; upd_val[nupd] = t; nupd++;
-                for (int64_t j = 0; j < d; j++) {
-                    int32_t x = vals[j];
-                    if (t < x && (!refined || x <= est[u]))
-                        next_active[col[row_ptr[u] + j]] = 1;
+                if (!refined)
+                    for (int64_t j = 0; j < d; j++)
+                        if (t < vals[j]) next_active[col[row_ptr[u] + j]] = 1;
+            }
+        }
+        for (int64_t i = 0; i < nupd; i++) {   /* write updates; keep old values */
+            int64_t u = upd_id[i];
+            int32_t t = upd_val[i];
+            upd_val[i] = est[u];
+            est[u] = t;
+        }
+        if (refined) {                          /* activation after the updates */
+            for (int64_t i = 0; i < nupd; i++) {
+                int64_t u = upd_id[i];
+                int32_t old_u = upd_val[i], new_u = est[u];
+                for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+                    int32_t x = est[col[e]];
+                    if (new_u < x && x <= old_u) next_active[col[e]] = 1;
                 }
             }
         }
-        for (int64_t i = 0; i < nupd; i++) est[upd_id[i]] = upd_val[i];
         for (int64_t v = 0; v < n; v++) {
             active[v] = next_active[v];
             next_active[v] = 0;
