@@ -1,0 +1,289 @@
+/*
+ * kcore.h -- C ABI of the GB300 k-core decomposition library.
+ *
+ * The library computes the coreness of every vertex of an undirected graph
+ * (Def. 1, Sec. II: core(v) is the largest k such that v belongs to the
+ * k-core, the inclusion-maximal vertex set inducing minimum degree >= k).
+ * It does so with the local iteration of Alg. 1 (Montresor et al.) as adapted
+ * to shared memory in Sec. IV (FastK): every estimate starts at the vertex's
+ * degree and is repeatedly lowered to the capped h-index of its neighbours'
+ * estimates; a vertex is re-evaluated only when a neighbour's new estimate
+ * falls below its own (selective sending, Sec. III-B).  Estimates never
+ * increase (the monotonicity the paper cites for dropping messages, Sec.
+ * III-B), which makes in-place asynchronous updates sound; the fixed point
+ * reached from the degrees is the coreness (Sec. III, convergence argument).
+ * All work runs in sm_103a CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions
+ *   - Vertex ids are int32 in [0, n), n < 2^31; degrees must be < 2^30.
+ *   - Return values are kcore_status: KCORE_OK (0), KCORE_PENDING (1) or a
+ *     negative error.  No C++ exception crosses this boundary.  After an
+ *     error, kcore_last_error() returns a message for the calling thread.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is ordered on that stream.
+ *   - Pointers are host pointers unless a flag says device.  The caller keeps
+ *     ownership of every array it passes; handles are owned by the library and
+ *     released with the matching destroy call.
+ *   - Functions taking a handle are not thread-safe on the same handle.
+ */
+#ifndef KCORE_H
+#define KCORE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t kcore_status;
+
+#define KCORE_OK                 0
+#define KCORE_PENDING            1   /* kcore_poll: result not ready yet            */
+#define KCORE_ERR_INVALID       -1   /* bad argument or malformed graph              */
+#define KCORE_ERR_OOM           -2   /* device or host allocation failed             */
+#define KCORE_ERR_CUDA          -3   /* a CUDA runtime call failed                   */
+#define KCORE_ERR_NOT_CONVERGED -4   /* sweep cap reached with vertices still active */
+#define KCORE_ERR_TIMEOUT       -5   /* a bounded device wait or a poll timed out    */
+#define KCORE_ERR_AGAIN         -6   /* admission refused: queue full / over budget  */
+#define KCORE_ERR_CANCELLED     -7   /* request was cancelled                        */
+
+/* ---- flags -------------------------------------------------------------- */
+#define KCORE_IN_DEVICE   (1u << 0)  /* input arrays are device pointers                 */
+#define KCORE_IN_CLEAN    (1u << 1)  /* input CSR is already symmetric, loop-free,
+                                        sorted ascending per row, without repeats     */
+#define KCORE_OUT_DEVICE  (1u << 2)  /* coreness_out is a device pointer                 */
+#define KCORE_SYNC_MODE   (1u << 3)  /* synchronous rounds (Alg. 3): every round reads a
+                                        snapshot of the estimates; deterministic per
+                                        round.  Default: in-place asynchronous sweeps */
+#define KCORE_REFINED     (1u << 4)  /* refined activation new_u < est(v) <= old_u (Sec.
+                                        IV, Further Optimizations); SYNC_MODE only     */
+#define KCORE_ASYNC       (1u << 5)  /* kcore_run returns once the work is enqueued;
+                                        kcore_wait() reports the status               */
+
+/* ---- options ------------------------------------------------------------ */
+/*
+ * Tuning knobs of the sweep engine.  Fill with kcore_default_options() and
+ * override fields; 0 in a field means "library default".  The degree tiers
+ * split the frontier by degree d: d <= t_lo is evaluated by one thread with a
+ * register histogram, t_lo < d <= t_hi by one warp, d > t_hi by one CTA with a
+ * shared-memory histogram.
+ */
+typedef struct kcore_options {
+    uint32_t struct_size;   /* sizeof(kcore_options)                                */
+    int32_t  t_lo;          /* thread-tier degree bound, 1..32 (default 16)          */
+    int32_t  t_hi;          /* warp-tier degree bound, t_lo..512 (default 512)       */
+    int32_t  block;         /* threads per CTA of the sweep kernel, 64..512, x32     */
+    int32_t  low_chunk;     /* thread tier: vertices per lane per work grab (1..8)   */
+    int32_t  med_chunk;     /* warp tier: vertices per warp per work grab (1..64)    */
+    int32_t  tail_max;      /* frontier size at or below which one CTA continues
+                               (default 1024; negative disables the tail)          */
+    int32_t  ctas_per_sm;   /* persistent CTAs per SM (0 = occupancy maximum)        */
+    int32_t  max_ctas;      /* cap on the persistent grid (0 = no cap)               */
+    int64_t  max_sweeps;    /* sweep cap (0 = 2m + n + 1, a hard bound: every
+                               productive sweep lowers the sum of estimates)       */
+    double   timeout_s;     /* budget of every bounded device wait (default 20 s)   */
+} kcore_options;
+
+/* Fill `opt` with the defaults. */
+void kcore_default_options(kcore_options* opt);
+
+/* ---- single graph ------------------------------------------------------- */
+typedef struct kcore_graph kcore_graph;   /* opaque, library-owned */
+
+/*
+ * kcore_create -- build a device graph from a CSR.
+ *   n             number of vertices (0 <= n < 2^31).
+ *   row_ptr       n+1 offsets, int32 or int64 per `row_ptr_bytes` (4 or 8);
+ *                 row_ptr[0] == 0, non-decreasing.  Row u lists the neighbours
+ *                 col_idx[row_ptr[u] .. row_ptr[u+1]).
+ *   col_idx       row_ptr[n] int32 vertex ids in [0, n).
+ *   flags         KCORE_IN_DEVICE (inputs are device pointers),
+ *                 KCORE_IN_CLEAN (skip cleaning; rows are checked to be strictly
+ *                 increasing and loop-free, symmetry is the caller's promise).
+ *   opt           NULL for defaults; copied.
+ * Without KCORE_IN_CLEAN the input may be directed, repeated or contain
+ * self-loops: the graph is cleaned on the device (Sec. IV-A: treated as
+ * undirected, self-loops removed; Sec. III-B: rows kept as sorted vectors):
+ * both directions of every pair, loops dropped, rows sorted, repeats removed.
+ * The cleaned CSR keeps the input's row_ptr width.  The call returns after the
+ * graph is built (it synchronises `cuda_stream`); the caller may free its
+ * arrays on return.  Errors: ERR_INVALID (n, width, offsets or ids out of
+ * range), ERR_OOM, ERR_CUDA.  *out is NULL on error.
+ */
+kcore_status kcore_create(int64_t n, const void* row_ptr, int32_t row_ptr_bytes,
+                          const int32_t* col_idx, uint32_t flags,
+                          const kcore_options* opt, void* cuda_stream, kcore_graph** out);
+
+/*
+ * kcore_create_coo -- build a device graph from raw edge samples.
+ *   n             number of vertices; nnz samples src[i] -> dst[i] (int32, in
+ *                 [0, n)), host or device per KCORE_IN_DEVICE.
+ *   row_ptr_bytes width of the cleaned CSR's row_ptr: 4 (needs 2m < 2^31) or 8.
+ * Every sample is an undirected edge; loops and repeats are removed as in
+ * kcore_create.  Other arguments, ownership and errors as kcore_create.
+ */
+kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const int32_t* dst,
+                              int32_t row_ptr_bytes, uint32_t flags, const kcore_options* opt,
+                              void* cuda_stream, kcore_graph** out);
+
+/*
+ * kcore_run -- compute the coreness of every vertex.
+ *   coreness_out  n int32 values, caller-owned; a host pointer, or a device
+ *                 pointer with KCORE_OUT_DEVICE.
+ *   flags         KCORE_OUT_DEVICE, KCORE_SYNC_MODE, KCORE_REFINED, KCORE_ASYNC.
+ * Each run starts from est = degree (Alg. 1 initialisation) and iterates on the
+ * device until no vertex is active; one persistent kernel runs every sweep.
+ * Without KCORE_ASYNC the call waits for the result and returns its status;
+ * with it, the call returns KCORE_OK once the work is enqueued on
+ * `cuda_stream` and kcore_wait() returns the run's status.
+ * Errors: ERR_INVALID (flags: KCORE_REFINED without KCORE_SYNC_MODE),
+ * ERR_NOT_CONVERGED (sweep cap hit; coreness_out then holds the current
+ * estimates, an upper bound of the coreness), ERR_TIMEOUT (a bounded device
+ * wait gave up), ERR_CUDA.
+ */
+kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, void* cuda_stream);
+
+/*
+ * kcore_set_options -- replace the graph's options (NULL = defaults).  A change
+ * of t_lo/t_hi re-splits the vertices into tiers on `cuda_stream` (synchronous).
+ * Errors: ERR_INVALID, ERR_CUDA.
+ */
+kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* cuda_stream);
+
+/* Wait for the last kcore_run on `g` and return its status. */
+kcore_status kcore_wait(kcore_graph* g);
+
+/* Sizes of the cleaned graph: vertices, directed CSR entries (2m), row_ptr width. */
+kcore_status kcore_graph_info(const kcore_graph* g, int64_t* n, int64_t* nnz,
+                              int32_t* row_ptr_bytes);
+
+/*
+ * kcore_copy_csr -- copy the cleaned CSR out (row_ptr in the graph's width,
+ * n+1 entries; col_idx nnz entries), to host buffers, or device buffers with
+ * KCORE_OUT_DEVICE.  Synchronous.
+ */
+kcore_status kcore_copy_csr(const kcore_graph* g, void* row_ptr_out, int32_t* col_idx_out,
+                            uint32_t flags);
+
+/*
+ * Statistics of the last run (synchronises with it).  Per-sweep counts follow
+ * Fig. 5 (activated vertices per iteration); bytes_algorithmic is what the
+ * method must move for the vertices it evaluated: per evaluated vertex u,
+ * 2 row_ptr entries + est[u] + deg(u) col_idx entries + deg(u) estimate
+ * gathers, plus 4 bytes per update.
+ */
+typedef struct kcore_run_stats {
+    int64_t n, nnz;             /* graph size (nnz = 2m)                              */
+    int64_t sweeps;             /* sweeps executed                                     */
+    int64_t tail_sweeps;        /* of which run by a single CTA                         */
+    int64_t evaluated;          /* sum over sweeps of the frontier size                */
+    int64_t edges_scanned;      /* sum over sweeps of the frontier's degrees           */
+    int64_t updates;            /* estimate decreases written                          */
+    int64_t pushes;             /* vertices added to a next frontier                   */
+    int64_t bytes_algorithmic;  /* see above                                           */
+    int32_t status;             /* status of the run                                   */
+    int32_t grid;               /* persistent CTAs launched                            */
+    int32_t block;              /* threads per CTA                                     */
+    int32_t row_ptr_bytes;
+    float   ms_create;          /* kcore_create device time (cleaning)                 */
+    float   ms_sweep;           /* sweep kernel device time                            */
+    float   ms_run;             /* whole kcore_run device time (init..output)          */
+} kcore_run_stats;
+
+kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out);
+
+/*
+ * Per-sweep trace of the last run: frontier size, frontier degree sum and
+ * updates for sweeps [0, min(cap, recorded)); *count gets the number written.
+ * Any output pointer may be NULL.
+ */
+kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsum,
+                               int64_t* updates, int64_t cap, int64_t* count);
+
+/* Release a graph (waits for its outstanding work).  NULL is ignored. */
+void kcore_destroy(kcore_graph* g);
+
+/* ---- batching and serving ------------------------------------------------ */
+/*
+ * A batch engine packs many graphs into one device arena and runs them
+ * together in persistent sweep launches (continuous batching): graphs that
+ * arrive while others are running are admitted, within the memory budget and
+ * slot limit, at the next sweep-chunk boundary; finished graphs leave and free
+ * their space.  The coreness is unique, so each graph's result is the same
+ * alone or in any mix.
+ */
+typedef struct kcore_batch kcore_batch;   /* opaque, library-owned */
+
+typedef struct kcore_serve_options {
+    uint32_t struct_size;     /* sizeof(kcore_serve_options)                          */
+    int64_t  mem_budget;      /* device bytes for the arena (0 = 4 GiB)               */
+    int32_t  max_slots;       /* graphs resident at once (0 = 4096)                   */
+    int32_t  max_queue;       /* queued, not yet admitted requests (0 = 1 << 20)      */
+    int32_t  chunk_sweeps;    /* sweeps per persistent launch (0 = 16)               */
+    int32_t  start_thread;    /* 1 = run the serving loop in a library thread;
+                                 0 = caller drives it with kcore_batch_step           */
+    kcore_options sweep;      /* sweep engine knobs (struct_size 0 = defaults)        */
+} kcore_serve_options;
+
+void kcore_default_serve_options(kcore_serve_options* opt);
+
+/* Create an engine; its CUDA stream is private.  Errors: ERR_INVALID, ERR_OOM, ERR_CUDA. */
+kcore_status kcore_batch_create(const kcore_serve_options* opt, kcore_batch** out);
+
+/*
+ * Queue one graph (raw CSR as in kcore_create, HOST arrays only, copied before
+ * return) and get a ticket.  Errors: ERR_INVALID; ERR_AGAIN when the queue is
+ * full or the graph can never fit the budget.
+ */
+kcore_status kcore_submit(kcore_batch* b, int64_t n, const void* row_ptr, int32_t row_ptr_bytes,
+                          const int32_t* col_idx, uint32_t flags, uint64_t* ticket);
+
+/* Same, from raw edge samples (host arrays). */
+kcore_status kcore_submit_coo(kcore_batch* b, int64_t n, int64_t nnz, const int32_t* src,
+                              const int32_t* dst, uint32_t flags, uint64_t* ticket);
+
+/*
+ * Wait up to timeout_us (0 = do not wait, < 0 = forever) for a ticket.  On
+ * KCORE_OK, n int32 coreness values are copied to the host buffer
+ * coreness_out (may be NULL to discard) and the ticket is released.  Returns
+ * KCORE_PENDING if not finished in time, ERR_CANCELLED, ERR_INVALID (unknown
+ * ticket), or the request's own error.
+ */
+kcore_status kcore_poll(kcore_batch* b, uint64_t ticket, int32_t* coreness_out, int64_t timeout_us);
+
+/* Cancel a queued or running request; its slot is freed at the next chunk. */
+kcore_status kcore_cancel(kcore_batch* b, uint64_t ticket);
+
+/*
+ * Drive the engine once (admit, one chunk of sweeps, retire) when it was
+ * created with start_thread = 0.  *active gets the number of graphs resident
+ * or queued afterwards.
+ */
+kcore_status kcore_batch_step(kcore_batch* b, int64_t* active);
+
+typedef struct kcore_batch_stats {
+    int64_t submitted, completed, cancelled, failed;
+    int64_t queued, resident;        /* right now                                      */
+    int64_t launches, sweeps;        /* persistent launches and sweeps run             */
+    int64_t arena_bytes, arena_used_peak;
+    double  latency_p50_ms, latency_p99_ms;   /* submit -> result ready, completed ones */
+    double  busy_s;                  /* wall time the engine spent with work resident  */
+} kcore_batch_stats;
+
+kcore_status kcore_batch_stats_get(kcore_batch* b, kcore_batch_stats* out);
+
+/* Stop the engine (cancels what is left) and release it.  NULL is ignored. */
+void kcore_batch_destroy(kcore_batch* b);
+
+/* ---- misc ----------------------------------------------------------------- */
+/* Message of the last error on the calling thread ("" if none). */
+const char* kcore_last_error(void);
+
+/* Library version string. */
+const char* kcore_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCORE_H */

@@ -1,0 +1,253 @@
+"""GB300 k-core decomposition: Python binding of libkcore (include/kcore.h).
+
+This layer only marshals arguments: numpy arrays are host pointers, CUDA
+torch tensors are device pointers, and torch's current stream is passed as the
+cudaStream_t.  Every step of the computation runs in the library's sm_103a
+kernels; there is no Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (KCORE_ASYNC, KCORE_ERR_AGAIN, KCORE_ERR_CANCELLED, KCORE_ERR_INVALID,
+                   KCORE_ERR_NOT_CONVERGED, KCORE_ERR_TIMEOUT, KCORE_IN_CLEAN, KCORE_IN_DEVICE,
+                   KCORE_OK, KCORE_OUT_DEVICE, KCORE_PENDING, KCORE_REFINED, KCORE_SYNC_MODE,
+                   SIGNATURES, BatchStats, KCoreError, Options, RunStats, ServeOptions, check, lib)
+
+__all__ = ["Graph", "BatchEngine", "default_options", "default_serve_options", "lib",
+           "KCoreError", "Options", "RunStats", "version"]
+
+
+def version() -> str:
+    return lib().kcore_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        torch = _torch()
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive, is_device) of a numpy array or torch tensor."""
+    if x is None:
+        return None, None, False
+    if _is_cuda_tensor(x):
+        torch = _torch()
+        want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            x = x.to(want).contiguous()
+        return x.data_ptr(), x, True
+    if hasattr(x, "numpy"):
+        x = x.numpy()
+    a = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+    return a.ctypes.data, a, False
+
+
+def default_options(**overrides) -> Options:
+    o = Options()
+    lib().kcore_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def default_serve_options(sweep: Options | None = None, **overrides) -> ServeOptions:
+    o = ServeOptions()
+    lib().kcore_default_serve_options(ctypes.byref(o))
+    if sweep is not None:
+        o.sweep = sweep
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown serve option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A cleaned graph resident on the GPU (kcore_create / kcore_create_coo)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        n, nnz, rp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        check(lib().kcore_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz),
+                                     ctypes.byref(rp)), "kcore_graph_info")
+        self.n, self.nnz, self.row_ptr_bytes = n.value, nnz.value, rp.value
+
+    # ---------------------------------------------------------------- create
+    @classmethod
+    def from_coo(cls, n: int, src, dst, row_ptr_bytes: int = 4, options: Options | None = None,
+                 stream=None) -> "Graph":
+        ps, ks, ds = _ptr(src, np.int32)
+        pd, kd, dd = _ptr(dst, np.int32)
+        if ds != dd:
+            raise ValueError("src and dst must both be host arrays or both CUDA tensors")
+        nnz = int(ks.shape[0]) if hasattr(ks, "shape") else int(ks.numel())
+        h = ctypes.c_void_p()
+        flags = KCORE_IN_DEVICE if ds else 0
+        check(lib().kcore_create_coo(n, nnz, ps, pd, row_ptr_bytes, flags,
+                                     ctypes.byref(options) if options else None,
+                                     _stream(stream), ctypes.byref(h)), "kcore_create_coo")
+        return cls(h.value)
+
+    @classmethod
+    def from_csr(cls, n: int, row_ptr, col_idx, clean: bool = False,
+                 options: Options | None = None, stream=None) -> "Graph":
+        rp_dtype = np.int64 if str(getattr(row_ptr, "dtype", "")).endswith("int64") else np.int32
+        pr, kr, dr = _ptr(row_ptr, rp_dtype)
+        pc, kc, dc = _ptr(col_idx, np.int32)
+        flags = (KCORE_IN_DEVICE if dr else 0) | (KCORE_IN_CLEAN if clean else 0)
+        h = ctypes.c_void_p()
+        check(lib().kcore_create(n, pr, 8 if rp_dtype == np.int64 else 4, pc, flags,
+                                 ctypes.byref(options) if options else None, _stream(stream),
+                                 ctypes.byref(h)), "kcore_create")
+        return cls(h.value)
+
+    # ---------------------------------------------------------------- run
+    def run(self, out=None, device: bool = True, sync_mode: bool = False, refined: bool = False,
+            wait: bool = True, stream=None, check_status: bool = True):
+        """Coreness of every vertex.  Returns `out` (allocated when None: an
+        int32 CUDA tensor if device else a numpy array)."""
+        if out is None:
+            if device:
+                torch = _torch()
+                out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+            else:
+                out = np.empty(self.n, dtype=np.int32)
+        is_dev = _is_cuda_tensor(out)
+        ptr = out.data_ptr() if is_dev else out.ctypes.data
+        flags = (KCORE_OUT_DEVICE if is_dev else 0) | (KCORE_SYNC_MODE if sync_mode else 0) | \
+            (KCORE_REFINED if refined else 0) | (0 if wait else KCORE_ASYNC)
+        st = lib().kcore_run(self._h, ptr, flags, _stream(stream))
+        if check_status:
+            check(st, "kcore_run")
+        self.last_status = st
+        return out
+
+    def wait(self) -> int:
+        return lib().kcore_wait(self._h)
+
+    def set_options(self, options: Options, stream=None) -> None:
+        check(lib().kcore_set_options(self._h, ctypes.byref(options), _stream(stream)),
+              "kcore_set_options")
+
+    def stats(self) -> dict:
+        s = RunStats()
+        check(lib().kcore_stats(self._h, ctypes.byref(s)), "kcore_stats")
+        return {k: getattr(s, k) for k, _ in RunStats._fields_}
+
+    def trace(self, cap: int = 1 << 16):
+        f = np.zeros(cap, np.int64)
+        d = np.zeros(cap, np.int64)
+        u = np.zeros(cap, np.int64)
+        cnt = ctypes.c_int64()
+        check(lib().kcore_sweep_trace(self._h, f.ctypes.data, d.ctypes.data, u.ctypes.data, cap,
+                                      ctypes.byref(cnt)), "kcore_sweep_trace")
+        k = cnt.value
+        return f[:k], d[:k], u[:k]
+
+    def csr(self):
+        """(row_ptr, col_idx) of the cleaned graph, as numpy arrays."""
+        rp = np.empty(self.n + 1, dtype=np.int64 if self.row_ptr_bytes == 8 else np.int32)
+        col = np.empty(max(self.nnz, 1), dtype=np.int32)
+        check(lib().kcore_copy_csr(self._h, rp.ctypes.data, col.ctypes.data, 0), "kcore_copy_csr")
+        return rp, col[: self.nnz]
+
+    def close(self) -> None:
+        if self._h and self._h.value:
+            lib().kcore_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchEngine:
+    """Continuous-batching engine (kcore_batch_*): submit graphs, poll results."""
+
+    def __init__(self, options: ServeOptions | None = None):
+        h = ctypes.c_void_p()
+        check(lib().kcore_batch_create(ctypes.byref(options) if options else None,
+                                       ctypes.byref(h)), "kcore_batch_create")
+        self._h = h
+
+    def submit_coo(self, n: int, src, dst) -> int:
+        ps, ks, _ = _ptr(src, np.int32)
+        pd, kd, _ = _ptr(dst, np.int32)
+        t = ctypes.c_uint64()
+        check(lib().kcore_submit_coo(self._h, n, int(ks.shape[0]), ps, pd, 0, ctypes.byref(t)),
+              "kcore_submit_coo")
+        return t.value
+
+    def submit_csr(self, n: int, row_ptr, col_idx, clean: bool = False) -> int:
+        rp_dtype = np.int64 if str(getattr(row_ptr, "dtype", "")).endswith("int64") else np.int32
+        pr, kr, _ = _ptr(row_ptr, rp_dtype)
+        pc, kc, _ = _ptr(col_idx, np.int32)
+        t = ctypes.c_uint64()
+        check(lib().kcore_submit(self._h, n, pr, 8 if rp_dtype == np.int64 else 4, pc,
+                                 KCORE_IN_CLEAN if clean else 0, ctypes.byref(t)), "kcore_submit")
+        return t.value
+
+    def poll(self, ticket: int, n: int | None = None, timeout_us: int = -1):
+        """(status, coreness or None).  status is KCORE_OK, KCORE_PENDING or an error."""
+        out = np.empty(max(n or 0, 1), dtype=np.int32) if n is not None else None
+        st = lib().kcore_poll(self._h, ticket, out.ctypes.data if out is not None else None,
+                              timeout_us)
+        if st == KCORE_OK:
+            return st, (out[:n] if out is not None else None)
+        return st, None
+
+    def cancel(self, ticket: int) -> int:
+        return lib().kcore_cancel(self._h, ticket)
+
+    def step(self) -> int:
+        a = ctypes.c_int64()
+        check(lib().kcore_batch_step(self._h, ctypes.byref(a)), "kcore_batch_step")
+        return a.value
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        check(lib().kcore_batch_stats_get(self._h, ctypes.byref(s)), "kcore_batch_stats_get")
+        return {k: getattr(s, k) for k, _ in BatchStats._fields_}
+
+    def close(self) -> None:
+        if self._h and self._h.value:
+            lib().kcore_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,539 @@
+// C ABI of the single-graph path: kcore_create*, kcore_run, stats, destroy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <string>
+
+#include "kc_common.cuh"
+
+namespace kc {
+cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cudaStream_t st);
+cudaError_t launch_output(const uint32_t* est, int* out, long long n, cudaStream_t st);
+
+static thread_local std::string t_err;
+
+void set_error(const std::string& msg) { t_err = msg; }
+
+kcore_status fail(kcore_status s, const std::string& msg) {
+    t_err = msg;
+    return s;
+}
+
+kcore_status cuda_status(cudaError_t e, const char* what) {
+    cudaGetLastError();
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? KCORE_ERR_OOM : KCORE_ERR_CUDA;
+}
+
+kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
+    kcore_default_options(out);
+    if (!in) return KCORE_OK;
+    if (in->struct_size != 0 && in->struct_size < sizeof(kcore_options))
+        return fail(KCORE_ERR_INVALID, "kcore_options.struct_size too small");
+    if (in->t_lo) out->t_lo = in->t_lo;
+    if (in->t_hi) out->t_hi = in->t_hi;
+    if (in->block) out->block = in->block;
+    if (in->low_chunk) out->low_chunk = in->low_chunk;
+    if (in->med_chunk) out->med_chunk = in->med_chunk;
+    if (in->tail_max) out->tail_max = in->tail_max;
+    if (in->ctas_per_sm) out->ctas_per_sm = in->ctas_per_sm;
+    if (in->max_ctas) out->max_ctas = in->max_ctas;
+    if (in->max_sweeps) out->max_sweeps = in->max_sweeps;
+    if (in->timeout_s > 0) out->timeout_s = in->timeout_s;
+    if (out->t_lo < 1 || out->t_lo > 32) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..32");
+    if (out->t_hi < out->t_lo || out->t_hi > 512)
+        return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..512");
+    if (out->block < 64 || out->block > 512 || out->block % 32)
+        return fail(KCORE_ERR_INVALID, "block must be a multiple of 32 in 64..512");
+    if (out->low_chunk < 1 || out->low_chunk > 8) return fail(KCORE_ERR_INVALID, "low_chunk 1..8");
+    if (out->med_chunk < 1 || out->med_chunk > 64) return fail(KCORE_ERR_INVALID, "med_chunk 1..64");
+    if (out->max_sweeps < 0 || out->ctas_per_sm < 0 || out->max_ctas < 0)
+        return fail(KCORE_ERR_INVALID, "negative option");
+    return KCORE_OK;
+}
+
+}  // namespace kc
+
+using namespace kc;
+
+struct kcore_graph {
+    int device = 0;
+    DevCsr csr;
+    kcore_options opt{};
+    uint32_t* est0 = nullptr;
+    uint32_t* est = nullptr;
+    int* init_list = nullptr;
+    int* list[2] = {nullptr, nullptr};
+    uint32_t* bitmap[2] = {nullptr, nullptr};
+    int* upd_list = nullptr;
+    int* upd_val = nullptr;
+    SweepCtl* ctl = nullptr;
+    long long* trace = nullptr;
+    long long max_trace = 0;
+    long long tier_cnt[kTiers] = {0, 0, 0};
+    SweepCtl* hctl = nullptr;  // pinned copy of the control block after a run
+    cudaEvent_t ev[6] = {};    // create0, create1, run0, sweep0, sweep1, run1
+    bool pending = false;
+    bool ran = false;
+    kcore_status last_status = KCORE_OK;
+    int last_grid = 0;
+    float ms_create = 0.f;
+};
+
+namespace {
+
+enum { EV_C0, EV_C1, EV_R0, EV_S0, EV_S1, EV_R1 };
+
+void release(kcore_graph* g) {
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    dfree(g->csr.row_ptr);
+    dfree(g->csr.col);
+    dfree(g->est0);
+    dfree(g->est);
+    dfree(g->init_list);
+    dfree(g->list[0]);
+    dfree(g->list[1]);
+    dfree(g->bitmap[0]);
+    dfree(g->bitmap[1]);
+    dfree(g->upd_list);
+    dfree(g->upd_val);
+    dfree(g->ctl);
+    dfree(g->trace);
+    if (g->hctl) cudaFreeHost(g->hctl);
+    for (auto& e : g->ev)
+        if (e) cudaEventDestroy(e);
+    cudaSetDevice(prev);
+    delete g;
+}
+
+// Allocates the per-run state and splits the vertices into degree tiers.
+kcore_status finish_graph(kcore_graph* g, cudaStream_t st) {
+    std::string err;
+    const int64_t n = g->csr.n;
+    const size_t words = (size_t)((n + 31) / 32);
+    kcore_status s;
+#define KC_ALLOC(ptr, bytes)                                    \
+    do {                                                        \
+        s = dmalloc((void**)&(ptr), (bytes), &err);             \
+        if (s != KCORE_OK) return fail(s, err);                 \
+    } while (0)
+    KC_ALLOC(g->est0, sizeof(uint32_t) * n);
+    KC_ALLOC(g->est, sizeof(uint32_t) * n);
+    KC_ALLOC(g->init_list, sizeof(int) * n);
+    KC_ALLOC(g->list[0], sizeof(int) * n);
+    KC_ALLOC(g->list[1], sizeof(int) * n);
+    KC_ALLOC(g->bitmap[0], sizeof(uint32_t) * words);
+    KC_ALLOC(g->bitmap[1], sizeof(uint32_t) * words);
+    KC_ALLOC(g->ctl, sizeof(SweepCtl));
+    g->max_trace = 1 << 16;
+    KC_ALLOC(g->trace, sizeof(long long) * 3 * g->max_trace);
+#undef KC_ALLOC
+    cudaError_t e = cudaMallocHost((void**)&g->hctl, sizeof(SweepCtl));
+    if (e != cudaSuccess) return cuda_status(e, "cudaMallocHost");
+    memset(g->hctl, 0, sizeof(SweepCtl));
+    s = tier_split(n, g->csr.row_ptr, g->csr.off_bytes, g->opt.t_lo, g->opt.t_hi, g->est0,
+                   g->init_list, g->tier_cnt, st, &err);
+    if (s != KCORE_OK) return fail(s, err);
+    return KCORE_OK;
+}
+
+kcore_status begin_create(int64_t n, int32_t row_ptr_bytes, const kcore_options* opt,
+                          kcore_graph** out, kcore_graph** g) {
+    if (!out) return fail(KCORE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > INT_MAX) return fail(KCORE_ERR_INVALID, "n must be in [0, 2^31)");
+    if (row_ptr_bytes != 4 && row_ptr_bytes != 8)
+        return fail(KCORE_ERR_INVALID, "row_ptr_bytes must be 4 or 8");
+    kcore_options o;
+    kcore_status s = normalize_options(opt, &o);
+    if (s != KCORE_OK) return s;
+    *g = new kcore_graph();
+    (*g)->opt = o;
+    cudaGetDevice(&(*g)->device);
+    for (auto& e : (*g)->ev) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            release(*g);
+            *g = nullptr;
+            return cuda_status(ce, "cudaEventCreate");
+        }
+    }
+    return KCORE_OK;
+}
+
+// Host input -> temporary device copy.
+template <typename T>
+kcore_status upload(const T* host, size_t count, cudaStream_t st, T** dev) {
+    cudaError_t e = cudaMallocAsync((void**)dev, std::max<size_t>(count, 1) * sizeof(T), st);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (input copy)");
+    if (count) {
+        e = cudaMemcpyAsync(*dev, host, count * sizeof(T), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMemcpyAsync (input copy)");
+    }
+    return KCORE_OK;
+}
+
+kcore_status wait_run(kcore_graph* g) {
+    if (!g->pending) return g->last_status;
+    g->pending = false;
+    cudaError_t e = cudaEventSynchronize(g->ev[EV_R1]);
+    if (e != cudaSuccess) {
+        g->last_status = cuda_status(e, "kcore_run");
+        return g->last_status;
+    }
+    const int st = g->hctl->status;
+    if (st != 0) {
+        g->last_status = (kcore_status)st;
+        if (st == KCORE_ERR_NOT_CONVERGED)
+            set_error("sweep cap reached before the frontier emptied");
+        else if (st == KCORE_ERR_TIMEOUT)
+            set_error("a device wait exceeded timeout_s");
+        else
+            set_error("sweep kernel reported an error");
+    } else if (!g->hctl->done) {
+        g->last_status = KCORE_ERR_CUDA;
+        set_error("sweep kernel ended without converging or reporting an error");
+    } else {
+        g->last_status = KCORE_OK;
+    }
+    return g->last_status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kcore_default_options(kcore_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(kcore_options);
+    o->t_lo = 16;
+    o->t_hi = 512;
+    o->block = 512;
+    o->low_chunk = 2;
+    o->med_chunk = 4;
+    o->tail_max = 1024;
+    o->ctas_per_sm = 0;
+    o->max_ctas = 0;
+    o->max_sweeps = 0;
+    o->timeout_s = 20.0;
+}
+
+const char* kcore_last_error(void) { return t_err.c_str(); }
+
+const char* kcore_version(void) { return "kcore-gb300 0.1 (sm_103a)"; }
+
+kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const int32_t* dst,
+                              int32_t row_ptr_bytes, uint32_t flags, const kcore_options* opt,
+                              void* cuda_stream, kcore_graph** out) {
+    kcore_graph* g = nullptr;
+    kcore_status s = begin_create(n, row_ptr_bytes, opt, out, &g);
+    if (s != KCORE_OK) return s;
+    if (nnz < 0 || (nnz > 0 && (!src || !dst))) {
+        release(g);
+        return fail(KCORE_ERR_INVALID, "bad edge arrays");
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaEventRecord(g->ev[EV_C0], st);
+    const int *ds = src, *dd = dst;
+    int *tmp_s = nullptr, *tmp_d = nullptr;
+    if (!(flags & KCORE_IN_DEVICE)) {
+        s = upload(src, (size_t)nnz, st, &tmp_s);
+        if (s == KCORE_OK) s = upload(dst, (size_t)nnz, st, &tmp_d);
+        ds = tmp_s;
+        dd = tmp_d;
+    }
+    std::string err;
+    if (s == KCORE_OK) {
+        s = clean_from_coo(n, nnz, ds, dd, row_ptr_bytes, st, &g->csr, &err);
+        if (s != KCORE_OK) set_error(err);
+    }
+    if (tmp_s) cudaFreeAsync(tmp_s, st);
+    if (tmp_d) cudaFreeAsync(tmp_d, st);
+    if (s == KCORE_OK) s = finish_graph(g, st);
+    if (s == KCORE_OK) {
+        cudaEventRecord(g->ev[EV_C1], st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_status(e, "kcore_create_coo");
+        else cudaEventElapsedTime(&g->ms_create, g->ev[EV_C0], g->ev[EV_C1]);
+    }
+    if (s != KCORE_OK) {
+        release(g);
+        return s;
+    }
+    *out = g;
+    return KCORE_OK;
+}
+
+kcore_status kcore_create(int64_t n, const void* row_ptr, int32_t row_ptr_bytes,
+                          const int32_t* col_idx, uint32_t flags, const kcore_options* opt,
+                          void* cuda_stream, kcore_graph** out) {
+    kcore_graph* g = nullptr;
+    kcore_status s = begin_create(n, row_ptr_bytes, opt, out, &g);
+    if (s != KCORE_OK) return s;
+    if (!row_ptr) {
+        release(g);
+        return fail(KCORE_ERR_INVALID, "row_ptr is NULL");
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaEventRecord(g->ev[EV_C0], st);
+    // nnz = row_ptr[n]
+    int64_t nnz = 0;
+    if (flags & KCORE_IN_DEVICE) {
+        long long tmp = 0;
+        cudaError_t e = cudaMemcpyAsync(&tmp, (const char*)row_ptr + (size_t)row_ptr_bytes * n,
+                                        row_ptr_bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            release(g);
+            return cuda_status(e, "read row_ptr[n]");
+        }
+        nnz = row_ptr_bytes == 8 ? tmp : (int64_t)(int32_t)(tmp & 0xffffffffLL);
+    } else {
+        nnz = row_ptr_bytes == 8 ? ((const int64_t*)row_ptr)[n] : ((const int32_t*)row_ptr)[n];
+    }
+    if (nnz < 0 || (nnz > 0 && !col_idx)) {
+        release(g);
+        return fail(KCORE_ERR_INVALID, "row_ptr[n] must be >= 0 and col_idx non-NULL");
+    }
+    const void* drp = row_ptr;
+    const int* dcol = col_idx;
+    void* tmp_rp = nullptr;
+    int* tmp_col = nullptr;
+    if (!(flags & KCORE_IN_DEVICE)) {
+        if (row_ptr_bytes == 8)
+            s = upload((const long long*)row_ptr, (size_t)n + 1, st, (long long**)&tmp_rp);
+        else
+            s = upload((const int*)row_ptr, (size_t)n + 1, st, (int**)&tmp_rp);
+        if (s == KCORE_OK) s = upload(col_idx, (size_t)nnz, st, &tmp_col);
+        drp = tmp_rp;
+        dcol = tmp_col;
+    }
+    std::string err;
+    if (s == KCORE_OK) {
+        if (flags & KCORE_IN_CLEAN) {
+            s = check_clean_csr(n, drp, row_ptr_bytes, dcol, nnz, st, &err);
+            if (s == KCORE_OK) s = dmalloc(&g->csr.row_ptr, (size_t)row_ptr_bytes * (n + 1), &err);
+            if (s == KCORE_OK) s = dmalloc((void**)&g->csr.col, sizeof(int) * nnz, &err);
+            if (s == KCORE_OK) {
+                cudaError_t e = cudaMemcpyAsync(g->csr.row_ptr, drp, (size_t)row_ptr_bytes * (n + 1),
+                                                cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess && nnz)
+                    e = cudaMemcpyAsync(g->csr.col, dcol, sizeof(int) * nnz,
+                                        cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) s = cuda_status(e, "copy clean CSR");
+                g->csr.n = n;
+                g->csr.nnz = nnz;
+                g->csr.off_bytes = row_ptr_bytes;
+            }
+        } else {
+            s = clean_from_csr(n, drp, row_ptr_bytes, dcol, nnz, row_ptr_bytes, st, &g->csr, &err);
+        }
+        if (s != KCORE_OK && !err.empty()) set_error(err);
+    }
+    if (tmp_rp) cudaFreeAsync(tmp_rp, st);
+    if (tmp_col) cudaFreeAsync(tmp_col, st);
+    if (s == KCORE_OK) s = finish_graph(g, st);
+    if (s == KCORE_OK) {
+        cudaEventRecord(g->ev[EV_C1], st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_status(e, "kcore_create");
+        else cudaEventElapsedTime(&g->ms_create, g->ev[EV_C0], g->ev[EV_C1]);
+    }
+    if (s != KCORE_OK) {
+        release(g);
+        return s;
+    }
+    *out = g;
+    return KCORE_OK;
+}
+
+kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* cuda_stream) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    kcore_options o;
+    kcore_status s = normalize_options(opt, &o);
+    if (s != KCORE_OK) return s;
+    s = wait_run(g);
+    (void)s;
+    const bool rebin = o.t_lo != g->opt.t_lo || o.t_hi != g->opt.t_hi;
+    g->opt = o;
+    if (!rebin) return KCORE_OK;
+    std::string err;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s = tier_split(g->csr.n, g->csr.row_ptr, g->csr.off_bytes, o.t_lo, o.t_hi, g->est0,
+                   g->init_list, g->tier_cnt, st, &err);
+    if (s != KCORE_OK) return fail(s, err);
+    return KCORE_OK;
+}
+
+kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, void* cuda_stream) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    if ((flags & KCORE_REFINED) && !(flags & KCORE_SYNC_MODE))
+        return fail(KCORE_ERR_INVALID, "KCORE_REFINED needs KCORE_SYNC_MODE");
+    const int64_t n = g->csr.n;
+    if (n > 0 && !coreness_out) return fail(KCORE_ERR_INVALID, "coreness_out is NULL");
+    if (g->pending) wait_run(g);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool sync_mode = (flags & KCORE_SYNC_MODE) != 0;
+    std::string err;
+    if (sync_mode && !g->upd_list) {
+        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err);
+        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err);
+        if (s != KCORE_OK) return fail(s, err);
+    }
+    const size_t words = (size_t)((n + 31) / 32);
+    cudaError_t e = cudaEventRecord(g->ev[EV_R0], st);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(g->est, g->est0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[0], 0xff, sizeof(uint32_t) * words, st);
+    if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[1], 0, sizeof(uint32_t) * words, st);
+    if (e == cudaSuccess) e = launch_ctl_init(g->ctl, g->tier_cnt, st);
+    if (e != cudaSuccess) return cuda_status(e, "kcore_run init");
+
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.row_ptr = g->csr.row_ptr;
+    a.col = g->csr.col;
+    a.est = g->est;
+    a.init_list = g->init_list;
+    a.list[0] = g->list[0];
+    a.list[1] = g->list[1];
+    a.bitmap[0] = g->bitmap[0];
+    a.bitmap[1] = g->bitmap[1];
+    a.upd_list = g->upd_list;
+    a.upd_val = g->upd_val;
+    a.tier_off[0] = 0;
+    a.tier_off[1] = g->tier_cnt[0];
+    a.tier_off[2] = g->tier_cnt[0] + g->tier_cnt[1];
+    a.ctl = g->ctl;
+    a.trace = g->trace;
+    a.max_trace = g->max_trace;
+    a.first_sweep = 0;
+    a.max_sweeps = g->opt.max_sweeps ? g->opt.max_sweeps : 2 * g->csr.nnz + n + 1;
+    a.stop_sweep = LLONG_MAX;
+    a.timeout_ns = (long long)(g->opt.timeout_s * 1e9);
+    a.n = (int)n;
+    a.t_lo = g->opt.t_lo;
+    a.t_hi = g->opt.t_hi;
+    a.low_chunk = g->opt.low_chunk;
+    a.med_chunk = g->opt.med_chunk;
+    a.tail_max = g->opt.tail_max < 0 ? 0 : g->opt.tail_max;
+    a.sync_mode = sync_mode ? 1 : 0;
+    a.refined = (flags & KCORE_REFINED) ? 1 : 0;
+    a.off64 = g->csr.off_bytes == 8 ? 1 : 0;
+
+    // Grid: enough CTAs for the first sweep's work, at most the co-resident maximum.
+    const long long work = n + g->csr.nnz;
+    long long want = (work + (long long)g->opt.block * 32 - 1) / ((long long)g->opt.block * 32);
+    want = std::max<long long>(1, want);
+    if (g->opt.max_ctas > 0) want = std::min<long long>(want, g->opt.max_ctas);
+    e = cudaEventRecord(g->ev[EV_S0], st);
+    if (e == cudaSuccess)
+        e = launch_sweep(a, g->opt.block, (int)std::min<long long>(want, INT_MAX), g->opt.ctas_per_sm,
+                         st, &g->last_grid);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev[EV_S1], st);
+    if (e != cudaSuccess) return cuda_status(e, "sweep launch");
+    if (flags & KCORE_OUT_DEVICE) {
+        e = launch_output(g->est, coreness_out, n, st);
+    } else {
+        e = launch_output(g->est, (int*)g->est, n, st);
+        if (e == cudaSuccess && n)
+            e = cudaMemcpyAsync(coreness_out, g->est, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->hctl, g->ctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev[EV_R1], st);
+    if (e != cudaSuccess) return cuda_status(e, "kcore_run output");
+    g->pending = true;
+    g->ran = true;
+    if (flags & KCORE_ASYNC) return KCORE_OK;
+    return wait_run(g);
+}
+
+kcore_status kcore_wait(kcore_graph* g) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    return wait_run(g);
+}
+
+kcore_status kcore_graph_info(const kcore_graph* g, int64_t* n, int64_t* nnz,
+                              int32_t* row_ptr_bytes) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    if (n) *n = g->csr.n;
+    if (nnz) *nnz = g->csr.nnz;
+    if (row_ptr_bytes) *row_ptr_bytes = g->csr.off_bytes;
+    return KCORE_OK;
+}
+
+kcore_status kcore_copy_csr(const kcore_graph* g, void* row_ptr_out, int32_t* col_idx_out,
+                            uint32_t flags) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    const cudaMemcpyKind kind =
+        (flags & KCORE_OUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (row_ptr_out)
+        e = cudaMemcpy(row_ptr_out, g->csr.row_ptr, (size_t)g->csr.off_bytes * (g->csr.n + 1), kind);
+    if (e == cudaSuccess && col_idx_out && g->csr.nnz)
+        e = cudaMemcpy(col_idx_out, g->csr.col, sizeof(int) * g->csr.nnz, kind);
+    if (e != cudaSuccess) return cuda_status(e, "kcore_copy_csr");
+    return KCORE_OK;
+}
+
+kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out) {
+    if (!g || !out) return fail(KCORE_ERR_INVALID, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->n = g->csr.n;
+    out->nnz = g->csr.nnz;
+    out->row_ptr_bytes = g->csr.off_bytes;
+    out->ms_create = g->ms_create;
+    out->block = g->opt.block;
+    if (!g->ran) return KCORE_OK;
+    kcore_status rs = wait_run(g);
+    const SweepCtl& c = *g->hctl;
+    out->status = rs;
+    out->sweeps = c.sweep;
+    out->tail_sweeps = c.tail_sweeps;
+    out->evaluated = (int64_t)c.tot[kAccEvaluated];
+    out->edges_scanned = (int64_t)c.tot[kAccDegsum];
+    out->updates = (int64_t)c.tot[kAccUpdates];
+    out->pushes = (int64_t)c.tot[kAccPushes];
+    out->bytes_algorithmic = out->evaluated * (2LL * g->csr.off_bytes + 4) +
+                             8LL * out->edges_scanned + 4LL * out->updates;
+    out->grid = g->last_grid;
+    cudaEventElapsedTime(&out->ms_sweep, g->ev[EV_S0], g->ev[EV_S1]);
+    cudaEventElapsedTime(&out->ms_run, g->ev[EV_R0], g->ev[EV_R1]);
+    return KCORE_OK;
+}
+
+kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsum,
+                               int64_t* updates, int64_t cap, int64_t* count) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    if (count) *count = 0;
+    if (!g->ran) return KCORE_OK;
+    wait_run(g);
+    const long long n = std::min<long long>({(long long)cap, g->hctl->sweep, g->max_trace});
+    if (n <= 0) return KCORE_OK;
+    long long* h = new long long[3 * n];
+    cudaError_t e = cudaMemcpy(h, g->trace, sizeof(long long) * 3 * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] h;
+        return cuda_status(e, "kcore_sweep_trace");
+    }
+    for (long long i = 0; i < n; i++) {
+        if (frontier) frontier[i] = h[3 * i];
+        if (degsum) degsum[i] = h[3 * i + 1];
+        if (updates) updates[i] = h[3 * i + 2];
+    }
+    delete[] h;
+    if (count) *count = n;
+    return KCORE_OK;
+}
+
+void kcore_destroy(kcore_graph* g) { release(g); }
+
+}  // extern "C"

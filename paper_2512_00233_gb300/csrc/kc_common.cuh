@@ -1,0 +1,116 @@
+// Internal declarations shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "kcore.h"
+
+namespace kc {
+
+// ---------------------------------------------------------------- estimates
+// Each estimate word holds the current coreness estimate in its low 30 bits
+// and the vertex's degree tier (0 thread, 1 warp, 2 CTA) in the top 2 bits, so
+// a push reads the tier of the neighbour from the same word it compares.
+constexpr uint32_t kEstBits = 30;
+constexpr uint32_t kEstMask = (1u << kEstBits) - 1u;
+constexpr int kTiers = 3;
+constexpr int kSlots = 3;        // rotating per-sweep counter slots
+constexpr int kHubBins = 4096;   // shared-memory histogram of the CTA tier
+
+// Accumulator indices of per-sweep statistics.
+enum { kAccEvaluated = 0, kAccDegsum = 1, kAccUpdates = 2, kAccPushes = 3, kAccN = 4 };
+
+// Control block of the persistent sweep kernel (device memory).  Slot s % 3
+// holds the frontier counts of sweep s; sweep s pushes into slot (s+1) % 3 and
+// the slot of sweep s-1 is cleared at the start of sweep s.
+struct SweepCtl {
+    unsigned int bar_count;          // grid barrier arrivals
+    unsigned int bar_gen;            // grid barrier generation
+    int status;                      // 0 or a negative kcore_status
+    int done;                        // 1 once the frontier is empty
+    long long sweep;                 // next sweep to run (resume point)
+    long long tail_sweeps;           // sweeps run by one CTA
+    unsigned int fcnt[kSlots][4];    // frontier size per tier
+    unsigned int cursor[kSlots][4];  // work cursor per tier
+    unsigned int ucnt[kSlots];       // synchronous mode: updates this sweep
+    unsigned int pad0;
+    unsigned long long acc[kSlots][kAccN];
+    unsigned long long tot[kAccN];
+    unsigned int tail_epoch;         // bumped when the single-CTA tail hands over
+    int tail_exit;                   // 1: launch over; 0: resume all CTAs
+    long long resume_sweep;
+};
+
+// Arguments of one persistent sweep launch.
+struct SweepArgs {
+    const void* row_ptr;             // int32 or int64 per off64
+    const int* col;
+    uint32_t* est;
+    const int* init_list;            // frontier of sweep 0 (tiers contiguous), or null
+    int* list[2];                    // frontier lists by sweep parity
+    uint32_t* bitmap[2];             // frontier membership by sweep parity
+    int* upd_list;                   // synchronous mode: updated vertices
+    int* upd_val;                    // synchronous mode: their new (then old) values
+    long long tier_off[kTiers];      // start of each tier inside a list
+    SweepCtl* ctl;
+    long long* trace;                // [max_trace][3]: frontier, degsum, updates
+    long long max_trace;
+    long long first_sweep;           // sweep index at which this launch starts
+    long long max_sweeps;            // NOT_CONVERGED at this sweep index
+    long long stop_sweep;            // this launch ends before this sweep index
+    long long timeout_ns;            // budget of every bounded wait
+    int n;
+    int t_lo, t_hi;
+    int low_chunk, med_chunk;
+    int tail_max;
+    int sync_mode, refined;
+    int off64;
+};
+
+// Launch the persistent sweep kernel (cooperative launch).  `grid` 0 picks the
+// occupancy maximum; the grid used is returned.
+cudaError_t launch_sweep(const SweepArgs& a, int block, int grid_req, int ctas_per_sm,
+                         cudaStream_t st, int* grid_used);
+
+// Largest cooperative grid for a block size.
+cudaError_t sweep_max_grid(int block, int t_lo, int t_hi, int off64, int* grid);
+
+// ---------------------------------------------------------------- CSR cleaning
+struct DevCsr {
+    int64_t n = 0, nnz = 0;
+    int off_bytes = 4;
+    void* row_ptr = nullptr;
+    int* col = nullptr;
+};
+
+// Raw samples (device) -> clean CSR (device, allocated here).  Returns a
+// kcore_status; on error *err names the problem.
+kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const int* dst,
+                            int off_bytes, cudaStream_t st, DevCsr* out, std::string* err);
+kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, const int* col,
+                            int64_t nnz, int off_bytes, cudaStream_t st, DevCsr* out,
+                            std::string* err);
+// Checks an already-clean device CSR (ids in range, rows strictly increasing,
+// no loops, offsets monotone).  KCORE_OK or ERR_INVALID.
+kcore_status check_clean_csr(int64_t n, const void* row_ptr, int off_bytes, const int* col,
+                             int64_t nnz, cudaStream_t st, std::string* err);
+
+// Tier split: est0 = (tier << 30) | degree, and the list of all vertices with
+// tiers contiguous and ids ascending inside each tier.  tier_cnt gets the
+// sizes.
+kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo, int t_hi,
+                        uint32_t* est0, int* init_list, long long tier_cnt[kTiers],
+                        cudaStream_t st, std::string* err);
+
+// Exclusive scan helper (device), out has N+1 entries when total_slot.
+cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,
+                            cudaStream_t st);
+
+// Device allocation helpers (report OOM separately from other CUDA errors).
+kcore_status dmalloc(void** p, size_t bytes, std::string* err);
+void dfree(void* p);
+
+}  // namespace kc
