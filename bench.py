@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the k-core hot path on GB300; prints ONE JSON line.
+
+A step is one pass of the whole path over one synthetic graph whose raw edge
+samples are already resident in HBM: device CSR cleaning (kcore_create_coo),
+estimate initialisation, the persistent sweep kernel until the frontier is
+empty, and the int32 coreness written to a device buffer (kcore_run).
+value = undirected edges m of the cleaned graph per second of step time.
+
+Also reported: the same metric end to end through the C ABI with host
+buffers (pinned host -> device copy of the samples and device -> host copy of
+the coreness inside the timed region), the decomposition alone on the
+resident graph (the paper's timing: load excluded, setup included), the sweep
+kernel's roofline fraction against the measured HBM copy bandwidth, the
+oracle on the host cores, and SM clocks sampled during the timed region.
+
+--impl reference times the oracle (plain C Batagelj-Zaversnik plus its host
+CSR build) on the host cores on the same workload and metric.
+
+Launch: python bench.py [--gpus 1] [--steps K] [--warmup W] [--workload NAME];
+for N > 1 under torch.distributed.run, each rank decomposes its own copy of
+the workload (independent replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decomposed edges/s"
+UNIT = "edges/s"
+L2_FLUSH_BYTES = 512 << 20
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="road2048")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi SM clock / throttle reasons sampled every 100 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = str(index)
+        try:
+            import torch
+            bus = getattr(torch.cuda.get_device_properties(index), "pci_bus_id", None)
+            if bus is not None:
+                dom = getattr(torch.cuda.get_device_properties(index), "pci_domain_id", 0)
+                dv = getattr(torch.cuda.get_device_properties(index), "pci_device_id", 0)
+                self.index = f"{dom:08X}:{bus:02X}:{dv:02X}.0"
+        except Exception:
+            pass
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.1)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("sweep.cu", "kc_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_00233_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per sweep-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("source_hash") == sweep_source_hash():
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- oracle on the host
+def oracle_pass(g):
+    import oracle
+    t0 = time.perf_counter()
+    rp, col = oracle.csr_build(g.n, g.src, g.dst)
+    core = oracle.coreness(g.n, rp, col)
+    dt = time.perf_counter() - t0
+    return dt, int(rp[-1]) // 2, core
+
+
+def oracle_sample(g, budget_s: float):
+    """The workload itself if one oracle pass fits the budget, else a prefix of
+    its samples sized to fit (same vertex set)."""
+    import graphgen
+    dt, m, _ = oracle_pass(graphgen.EdgeList(g.n, g.src[:1 << 16], g.dst[:1 << 16]))
+    per_sample = max(dt, 1e-4) / min(g.samples, 1 << 16)
+    est = per_sample * g.samples + 1e-8 * g.n
+    if est <= budget_s:
+        return g, "full workload"
+    k = max(1 << 16, int(budget_s / per_sample))
+    return (graphgen.EdgeList(g.n, g.src[:k], g.dst[:k]),
+            f"first {k} of {g.samples} edge samples (same vertex set)")
+
+
+def cpu_baseline(g, budget_s: float):
+    sample, desc = oracle_sample(g, budget_s / 2)
+    times, m = [], 0
+    t_start = time.perf_counter()
+    while True:
+        dt, m, _ = oracle_pass(sample)
+        times.append(dt)
+        if time.perf_counter() - t_start > budget_s / 2 or len(times) >= 5:
+            break
+    v = m / statistics.mean(times)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{desc}; {len(times)} pass(es) of host CSR build + Batagelj-Zaversnik, "
+                      f"single thread, mean {statistics.mean(times):.3f} s per pass"}
+
+
+def run_reference(args):
+    import graphgen
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    g = graphgen.workload(args.workload)
+    sample, desc = oracle_sample(g, 3.0)
+    for _ in range(args.warmup):
+        oracle_pass(sample)
+    times, m = [], 0
+    for _ in range(args.steps):
+        dt, m, _ = oracle_pass(sample)
+        times.append(dt)
+    total = sum(times)
+    value = m * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": g.name, "n": g.n, "samples": g.samples, "m": m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{desc}; host CSR build + Batagelj-Zaversnik per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2512_00233_gb300 as K
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    g0 = graphgen.workload(args.workload)
+    rp_bytes = g0.meta["row_ptr_bytes"]
+    src_d = torch.from_numpy(g0.src).to(dev)
+    dst_d = torch.from_numpy(g0.dst).to(dev)
+    out_d = torch.empty(g0.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def flush_l2():
+        flush.add_(1)
+
+    def step_device():
+        g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes)
+        g.run(out=out_d)
+        return g
+
+    # warm-up (also gives m and the per-run statistics)
+    for _ in range(args.warmup):
+        flush_l2()
+        step_device().close()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K whole steps, device-resident inputs
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    launches0 = K.lib().kcore_kernel_launches()
+    with ClockSampler(dev) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush_l2()
+            ev[i][0].record(stream)
+            g = step_device()
+            ev[i][1].record(stream)
+            stats.append(g.stats())      # waits for the step; outside the event pair
+            g.close()
+        torch.cuda.synchronize()
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    launches = (K.lib().kcore_kernel_launches() - launches0) / args.steps
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    m = stats[0]["nnz"] // 2
+    local_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    total_s = local_ms / 1e3
+    value = m * args.steps * ws / total_s
+
+    # ---- decomposition alone on the resident graph (paper's timing)
+    g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes)
+    run_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    sweep_stats = []
+    for _ in range(2):
+        flush_l2()
+        g.run(out=out_d)
+    for i in range(args.steps):
+        flush_l2()
+        run_ev[i][0].record(stream)
+        g.run(out=out_d)
+        run_ev[i][1].record(stream)
+        sweep_stats.append(g.stats())
+    torch.cuda.synchronize()
+    run_ms = [a.elapsed_time(b) for a, b in run_ev]
+    g.close()
+
+    # ---- end to end through the C ABI with host buffers
+    src_h = torch.from_numpy(g0.src).pin_memory()
+    dst_h = torch.from_numpy(g0.dst).pin_memory()
+    out_h = torch.empty(g0.n, dtype=torch.int32).pin_memory()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        flush_l2()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gh = K.Graph.from_coo(g0.n, src_h.numpy(), dst_h.numpy(), rp_bytes)
+        gh.run(out=out_h.numpy())
+        t1 = time.perf_counter()
+        gh.close()
+        if i >= args.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_value = m * ws / statistics.mean(e2e_t)
+
+    # ---- roofline of the sweep kernel (dominant kernel of the decomposition)
+    peak, peak_kind = measured_peaks()
+    bytes_alg = statistics.mean(s["bytes_algorithmic"] for s in sweep_stats)
+    sweep_ms = statistics.mean(s["ms_sweep"] for s in sweep_stats)
+    achieved = bytes_alg / (sweep_ms / 1e3) / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    line = None
+    if rank == 0:
+        create_ms = statistics.mean(s["ms_create"] for s in stats)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": local_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": g0.name, "n": g0.n, "samples": g0.samples, "m": m,
+                       "row_ptr_bytes": rp_bytes, "l2": "512 MiB buffer rewritten between steps",
+                       "step": "kcore_create_coo (device samples) + kcore_run (device output)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * g0.samples,
+                    "d2h_bytes_per_step": 4 * g0.n},
+            "gpu_launches": launches,
+            "decompose": {"value": m / (statistics.mean(run_ms) / 1e3), "unit": UNIT,
+                          "ms_run": statistics.mean(run_ms), "ms_sweep": sweep_ms,
+                          "ms_create": create_ms,
+                          "sweeps": statistics.mean(s["sweeps"] for s in sweep_stats),
+                          "tail_sweeps": statistics.mean(s["tail_sweeps"] for s in sweep_stats),
+                          "evaluated": statistics.mean(s["evaluated"] for s in sweep_stats),
+                          "edges_scanned": statistics.mean(s["edges_scanned"] for s in sweep_stats),
+                          "grid": sweep_stats[0]["grid"], "block": sweep_stats[0]["block"]},
+            "roofline": {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "bytes_per_launch": bytes_alg},
+            "clocks": clocks.summary(),
+            "wall_s": t_wall,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g0, args.cpu_budget_s)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -55,8 +55,11 @@ typedef int32_t kcore_status;
 #define KCORE_SYNC_MODE   (1u << 3)  /* synchronous rounds (Alg. 3): every round reads a
                                         snapshot of the estimates; deterministic per
                                         round.  Default: in-place asynchronous sweeps */
-#define KCORE_REFINED     (1u << 4)  /* refined activation new_u < est(v) <= old_u (Sec.
-                                        IV, Further Optimizations); SYNC_MODE only     */
+#define KCORE_REFINED     (1u << 4)  /* refined activation (Sec. IV, Further
+                                        Optimizations): u re-activates v only if
+                                        new_u < est(v) <= old_u; in asynchronous mode
+                                        also when v is in the current frontier (its
+                                        read of est(v) may be stale)                  */
 #define KCORE_ASYNC       (1u << 5)  /* kcore_run returns once the work is enqueued;
                                         kcore_wait() reports the status               */
 
@@ -70,8 +73,8 @@ typedef int32_t kcore_status;
  */
 typedef struct kcore_options {
     uint32_t struct_size;   /* sizeof(kcore_options)                                */
-    int32_t  t_lo;          /* thread-tier degree bound, 1..32 (default 16)          */
-    int32_t  t_hi;          /* warp-tier degree bound, t_lo..512 (default 512)       */
+    int32_t  t_lo;          /* thread-tier degree bound, 1..16 (default 16)          */
+    int32_t  t_hi;          /* warp-tier degree bound, t_lo..256 (default 256)       */
     int32_t  block;         /* threads per CTA of the sweep kernel, 64..512, x32     */
     int32_t  low_chunk;     /* thread tier: vertices per lane per work grab (1..8)   */
     int32_t  med_chunk;     /* warp tier: vertices per warp per work grab (1..64)    */
@@ -136,8 +139,7 @@ kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const 
  * Without KCORE_ASYNC the call waits for the result and returns its status;
  * with it, the call returns KCORE_OK once the work is enqueued on
  * `cuda_stream` and kcore_wait() returns the run's status.
- * Errors: ERR_INVALID (flags: KCORE_REFINED without KCORE_SYNC_MODE),
- * ERR_NOT_CONVERGED (sweep cap hit; coreness_out then holds the current
+ * Errors: ERR_INVALID (NULL arguments), ERR_NOT_CONVERGED (sweep cap hit; coreness_out then holds the current
  * estimates, an upper bound of the coreness), ERR_TIMEOUT (a bounded device
  * wait gave up), ERR_CUDA.
  */
@@ -193,12 +195,13 @@ typedef struct kcore_run_stats {
 kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out);
 
 /*
- * Per-sweep trace of the last run: frontier size, frontier degree sum and
- * updates for sweeps [0, min(cap, recorded)); *count gets the number written.
- * Any output pointer may be NULL.
+ * Per-sweep trace of the last run: frontier size, frontier degree sum,
+ * updates, and the sweep's start time in ns after the first sweep's start
+ * (device globaltimer), for sweeps [0, min(cap, recorded)); *count gets the
+ * number written.  Any output pointer may be NULL.
  */
 kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsum,
-                               int64_t* updates, int64_t cap, int64_t* count);
+                               int64_t* updates, int64_t* start_ns, int64_t cap, int64_t* count);
 
 /* Release a graph (waits for its outstanding work).  NULL is ignored. */
 void kcore_destroy(kcore_graph* g);
@@ -281,6 +284,15 @@ const char* kcore_last_error(void);
 
 /* Library version string. */
 const char* kcore_version(void);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t kcore_kernel_launches(void);
+
+/*
+ * Device memory freed by the library stays cached in its per-device memory
+ * pool for reuse by later graphs; this returns the cached blocks to the driver.
+ */
+void kcore_release_cached_memory(void);
 
 #ifdef __cplusplus
 }

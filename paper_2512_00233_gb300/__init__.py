@@ -152,14 +152,18 @@ class Graph:
         check(lib().kcore_stats(self._h, ctypes.byref(s)), "kcore_stats")
         return {k: getattr(s, k) for k, _ in RunStats._fields_}
 
-    def trace(self, cap: int = 1 << 16):
+    def trace(self, cap: int = 1 << 16, with_time: bool = False):
+        """Per-sweep (frontier size, frontier degree sum, updates[, start ns])."""
         f = np.zeros(cap, np.int64)
         d = np.zeros(cap, np.int64)
         u = np.zeros(cap, np.int64)
+        t = np.zeros(cap, np.int64)
         cnt = ctypes.c_int64()
-        check(lib().kcore_sweep_trace(self._h, f.ctypes.data, d.ctypes.data, u.ctypes.data, cap,
-                                      ctypes.byref(cnt)), "kcore_sweep_trace")
+        check(lib().kcore_sweep_trace(self._h, f.ctypes.data, d.ctypes.data, u.ctypes.data,
+                                      t.ctypes.data, cap, ctypes.byref(cnt)), "kcore_sweep_trace")
         k = cnt.value
+        if with_time:
+            return f[:k], d[:k], u[:k], t[:k]
         return f[:k], d[:k], u[:k]
 
     def csr(self):

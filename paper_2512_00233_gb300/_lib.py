@@ -84,7 +84,7 @@ SIGNATURES = {
                                  ctypes.POINTER(c_i32)]),
     "kcore_copy_csr": (c_i32, [c_vp, c_vp, c_vp, c_u32]),
     "kcore_stats": (c_i32, [c_vp, ctypes.POINTER(RunStats)]),
-    "kcore_sweep_trace": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
+    "kcore_sweep_trace": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "kcore_destroy": (None, [c_vp]),
     "kcore_default_serve_options": (None, [ctypes.POINTER(ServeOptions)]),
     "kcore_batch_create": (c_i32, [ctypes.POINTER(ServeOptions), ctypes.POINTER(c_vp)]),
@@ -97,6 +97,8 @@ SIGNATURES = {
     "kcore_batch_destroy": (None, [c_vp]),
     "kcore_last_error": (ctypes.c_char_p, []),
     "kcore_version": (ctypes.c_char_p, []),
+    "kcore_kernel_launches": (c_i64, []),
+    "kcore_release_cached_memory": (None, []),
 }
 
 _lib = None

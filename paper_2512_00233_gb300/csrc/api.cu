@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
 #include <string>
@@ -13,6 +14,10 @@ cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cud
 cudaError_t launch_output(const uint32_t* est, int* out, long long n, cudaStream_t st);
 
 static thread_local std::string t_err;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { t_err = msg; }
 
@@ -43,8 +48,9 @@ kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
     if (in->max_sweeps) out->max_sweeps = in->max_sweeps;
     if (in->timeout_s > 0) out->timeout_s = in->timeout_s;
     if (out->t_lo < 1 || out->t_lo > 32) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..32");
-    if (out->t_hi < out->t_lo || out->t_hi > 512)
-        return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..512");
+    if (out->t_hi < out->t_lo || out->t_hi > 256)
+        return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..256");
+    if (out->t_lo > 16) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..16");
     if (out->block < 64 || out->block > 512 || out->block % 32)
         return fail(KCORE_ERR_INVALID, "block must be a multiple of 32 in 64..512");
     if (out->low_chunk < 1 || out->low_chunk > 8) return fail(KCORE_ERR_INVALID, "low_chunk 1..8");
@@ -65,8 +71,8 @@ struct kcore_graph {
     uint32_t* est0 = nullptr;
     uint32_t* est = nullptr;
     int* init_list = nullptr;
-    int* list[2] = {nullptr, nullptr};
-    uint32_t* bitmap[2] = {nullptr, nullptr};
+    int* list[kParities] = {nullptr, nullptr, nullptr};
+    uint32_t* bitmap[kParities] = {nullptr, nullptr, nullptr};
     int* upd_list = nullptr;
     int* upd_val = nullptr;
     SweepCtl* ctl = nullptr;
@@ -97,15 +103,15 @@ void release(kcore_graph* g) {
     dfree(g->est0);
     dfree(g->est);
     dfree(g->init_list);
-    dfree(g->list[0]);
-    dfree(g->list[1]);
-    dfree(g->bitmap[0]);
-    dfree(g->bitmap[1]);
+    for (int p = 0; p < kParities; p++) {
+        dfree(g->list[p]);
+        dfree(g->bitmap[p]);
+    }
     dfree(g->upd_list);
     dfree(g->upd_val);
     dfree(g->ctl);
     dfree(g->trace);
-    if (g->hctl) cudaFreeHost(g->hctl);
+    if (g->hctl) pinned_put(g->hctl);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     cudaSetDevice(prev);
@@ -120,22 +126,23 @@ kcore_status finish_graph(kcore_graph* g, cudaStream_t st) {
     kcore_status s;
 #define KC_ALLOC(ptr, bytes)                                    \
     do {                                                        \
-        s = dmalloc((void**)&(ptr), (bytes), &err);             \
+        s = dmalloc((void**)&(ptr), (bytes), &err, st);         \
         if (s != KCORE_OK) return fail(s, err);                 \
     } while (0)
     KC_ALLOC(g->est0, sizeof(uint32_t) * n);
     KC_ALLOC(g->est, sizeof(uint32_t) * n);
     KC_ALLOC(g->init_list, sizeof(int) * n);
-    KC_ALLOC(g->list[0], sizeof(int) * n);
-    KC_ALLOC(g->list[1], sizeof(int) * n);
-    KC_ALLOC(g->bitmap[0], sizeof(uint32_t) * words);
-    KC_ALLOC(g->bitmap[1], sizeof(uint32_t) * words);
+    for (int p = 0; p < kParities; p++) {
+        KC_ALLOC(g->list[p], sizeof(int) * n);
+        KC_ALLOC(g->bitmap[p], sizeof(uint32_t) * words);
+    }
     KC_ALLOC(g->ctl, sizeof(SweepCtl));
     g->max_trace = 1 << 16;
-    KC_ALLOC(g->trace, sizeof(long long) * 3 * g->max_trace);
+    KC_ALLOC(g->trace, sizeof(long long) * 4 * g->max_trace);
 #undef KC_ALLOC
-    cudaError_t e = cudaMallocHost((void**)&g->hctl, sizeof(SweepCtl));
-    if (e != cudaSuccess) return cuda_status(e, "cudaMallocHost");
+    static_assert(sizeof(SweepCtl) <= kPinnedBlock, "control block copy does not fit");
+    cudaError_t e = pinned_get((void**)&g->hctl, sizeof(SweepCtl));
+    if (e != cudaSuccess) return cuda_status(e, "pinned host block");
     memset(g->hctl, 0, sizeof(SweepCtl));
     s = tier_split(n, g->csr.row_ptr, g->csr.off_bytes, g->opt.t_lo, g->opt.t_hi, g->est0,
                    g->init_list, g->tier_cnt, st, &err);
@@ -214,9 +221,9 @@ void kcore_default_options(kcore_options* o) {
     memset(o, 0, sizeof(*o));
     o->struct_size = sizeof(kcore_options);
     o->t_lo = 16;
-    o->t_hi = 512;
+    o->t_hi = 256;
     o->block = 512;
-    o->low_chunk = 2;
+    o->low_chunk = 8;
     o->med_chunk = 4;
     o->tail_max = 1024;
     o->ctas_per_sm = 0;
@@ -228,6 +235,8 @@ void kcore_default_options(kcore_options* o) {
 const char* kcore_last_error(void) { return t_err.c_str(); }
 
 const char* kcore_version(void) { return "kcore-gb300 0.1 (sm_103a)"; }
+
+int64_t kcore_kernel_launches(void) { return (int64_t)launches(); }
 
 kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const int32_t* dst,
                               int32_t row_ptr_bytes, uint32_t flags, const kcore_options* opt,
@@ -319,8 +328,8 @@ kcore_status kcore_create(int64_t n, const void* row_ptr, int32_t row_ptr_bytes,
     if (s == KCORE_OK) {
         if (flags & KCORE_IN_CLEAN) {
             s = check_clean_csr(n, drp, row_ptr_bytes, dcol, nnz, st, &err);
-            if (s == KCORE_OK) s = dmalloc(&g->csr.row_ptr, (size_t)row_ptr_bytes * (n + 1), &err);
-            if (s == KCORE_OK) s = dmalloc((void**)&g->csr.col, sizeof(int) * nnz, &err);
+            if (s == KCORE_OK) s = dmalloc(&g->csr.row_ptr, (size_t)row_ptr_bytes * (n + 1), &err, st);
+            if (s == KCORE_OK) s = dmalloc((void**)&g->csr.col, sizeof(int) * nnz, &err, st);
             if (s == KCORE_OK) {
                 cudaError_t e = cudaMemcpyAsync(g->csr.row_ptr, drp, (size_t)row_ptr_bytes * (n + 1),
                                                 cudaMemcpyDeviceToDevice, st);
@@ -374,8 +383,6 @@ kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* c
 
 kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, void* cuda_stream) {
     if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
-    if ((flags & KCORE_REFINED) && !(flags & KCORE_SYNC_MODE))
-        return fail(KCORE_ERR_INVALID, "KCORE_REFINED needs KCORE_SYNC_MODE");
     const int64_t n = g->csr.n;
     if (n > 0 && !coreness_out) return fail(KCORE_ERR_INVALID, "coreness_out is NULL");
     if (g->pending) wait_run(g);
@@ -383,8 +390,8 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
     const bool sync_mode = (flags & KCORE_SYNC_MODE) != 0;
     std::string err;
     if (sync_mode && !g->upd_list) {
-        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err);
-        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err);
+        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
+        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
         if (s != KCORE_OK) return fail(s, err);
     }
     const size_t words = (size_t)((n + 31) / 32);
@@ -393,6 +400,7 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
         e = cudaMemcpyAsync(g->est, g->est0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[0], 0xff, sizeof(uint32_t) * words, st);
     if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[1], 0, sizeof(uint32_t) * words, st);
+    if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[2], 0, sizeof(uint32_t) * words, st);
     if (e == cudaSuccess) e = launch_ctl_init(g->ctl, g->tier_cnt, st);
     if (e != cudaSuccess) return cuda_status(e, "kcore_run init");
 
@@ -402,10 +410,11 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
     a.col = g->csr.col;
     a.est = g->est;
     a.init_list = g->init_list;
-    a.list[0] = g->list[0];
-    a.list[1] = g->list[1];
-    a.bitmap[0] = g->bitmap[0];
-    a.bitmap[1] = g->bitmap[1];
+    for (int p = 0; p < kParities; p++) {
+        a.list[p] = g->list[p];
+        a.bitmap[p] = g->bitmap[p];
+    }
+    a.words = (long long)words;
     a.upd_list = g->upd_list;
     a.upd_val = g->upd_val;
     a.tier_off[0] = 0;
@@ -511,23 +520,24 @@ kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out) {
 }
 
 kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsum,
-                               int64_t* updates, int64_t cap, int64_t* count) {
+                               int64_t* updates, int64_t* start_ns, int64_t cap, int64_t* count) {
     if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
     if (count) *count = 0;
     if (!g->ran) return KCORE_OK;
     wait_run(g);
     const long long n = std::min<long long>({(long long)cap, g->hctl->sweep, g->max_trace});
     if (n <= 0) return KCORE_OK;
-    long long* h = new long long[3 * n];
-    cudaError_t e = cudaMemcpy(h, g->trace, sizeof(long long) * 3 * n, cudaMemcpyDeviceToHost);
+    long long* h = new long long[4 * n];
+    cudaError_t e = cudaMemcpy(h, g->trace, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         delete[] h;
         return cuda_status(e, "kcore_sweep_trace");
     }
     for (long long i = 0; i < n; i++) {
-        if (frontier) frontier[i] = h[3 * i];
-        if (degsum) degsum[i] = h[3 * i + 1];
-        if (updates) updates[i] = h[3 * i + 2];
+        if (frontier) frontier[i] = h[4 * i];
+        if (degsum) degsum[i] = h[4 * i + 1];
+        if (updates) updates[i] = h[4 * i + 2];
+        if (start_ns) start_ns[i] = h[4 * i + 3] - h[3];
     }
     delete[] h;
     if (count) *count = n;

@@ -2,16 +2,21 @@
 // removed; Sec. III-B: neighbour lists kept as sorted vectors).
 //
 // Pipeline, all on the device:
-//   1. expand   every sample (u, v), u != v, becomes the two 64-bit keys
-//               (u << 32 | v) and (v << 32 | u); loops become a sentinel that
-//               sorts last.
-//   2. sort     stable LSD radix sort, 8-bit digits, only over the bits that
-//               vertex ids use (reduce-then-scan per digit; stable in-tile
-//               ranking with __match_any_sync).
-//   3. dedupe   keep a key when it differs from its predecessor; an exclusive
-//               scan of the keep flags gives its position in col_idx.
-//   4. rows     the first and last entry of every row give its degree; an
-//               exclusive scan of the degrees gives row_ptr.
+//   1. count    every sample (u, v) with u != v adds one to deg(u) and deg(v)
+//               (atomics); ids outside [0, n) raise a flag and are skipped.
+//   2. offsets  exclusive scan of the counts: the segment of each row.
+//   3. scatter  each sample writes v into u's segment and u into v's, at a slot
+//               taken with an atomic on the row's fill counter (unordered).
+//   4. sort     each segment is sorted and its repeats dropped in place, by a
+//               size class: one thread with a register sorting network (<= 32
+//               entries), one warp with a register bitonic sort (<= 1024), one
+//               CTA with a shared-memory bitonic sort (<= 16384), and, for the
+//               few larger hub rows, a stable LSD radix sort of 64-bit
+//               (row rank, column) keys over the whole GPU.
+//   5. rows     exclusive scan of the distinct counts gives row_ptr; the
+//               sorted distinct prefixes are copied into col_idx.
+// The host waits three times: for the entry count, for the size classes, and
+// at the end for the sizes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,7 +30,9 @@ namespace kc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned long long kSentinel = ~0ull;
+constexpr uint32_t kPad = 0xffffffffu;       // sorts after every vertex id
+constexpr int kSmallMax = 32, kMidMax = 1024, kBigMax = 16384;
+constexpr int kBigT = 1024;
 
 // ------------------------------------------------------------------ scan
 constexpr int kScanT = 512, kScanI = 8, kScanTile = kScanT * kScanI;
@@ -112,18 +119,24 @@ cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStre
     if (nb == 1) {
         k_scan_down<<<1, kScanT, 0, st>>>(f, N, (const unsigned long long*)nullptr, out,
                                           with_total ? 1 : 0);
+        count_launch();
         return cudaGetLastError();
     }
     unsigned long long *bsum = nullptr, *boff = nullptr;
     cudaError_t e = cudaMallocAsync(&bsum, sizeof(unsigned long long) * nb, st);
     if (e != cudaSuccess) return e;
     e = cudaMallocAsync(&boff, sizeof(unsigned long long) * (nb + 1), st);
-    if (e != cudaSuccess) { cudaFreeAsync(bsum, st); return e; }
+    if (e != cudaSuccess) {
+        cudaFreeAsync(bsum, st);
+        return e;
+    }
     k_scan_reduce<<<(unsigned)nb, kScanT, 0, st>>>(f, N, bsum);
+    count_launch();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan(ReadU64{bsum}, nb, boff, false, st);
     if (e == cudaSuccess) {
         k_scan_down<<<(unsigned)nb, kScanT, 0, st>>>(f, N, boff, out, with_total ? 1 : 0);
+        count_launch();
         e = cudaGetLastError();
     }
     cudaFreeAsync(bsum, st);
@@ -131,57 +144,316 @@ cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStre
     return e;
 }
 
-// ------------------------------------------------------------------ expand
-__global__ void k_expand_coo(const int* __restrict__ src, const int* __restrict__ dst, long long S,
-                             int n, unsigned long long* __restrict__ keys, int* bad) {
+// ------------------------------------------------------------------ count / scatter
+// Build state on the device: the error flag and the class lists of the rows
+// that one thread does not sort.
+struct BuildCtl {
+    int bad;               // an id or offset out of range
+    unsigned n_mid, n_big, n_huge;
+    unsigned long long huge_entries;
+};
+
+__global__ void k_count_coo(const int* __restrict__ src, const int* __restrict__ dst, long long S,
+                            int n, uint32_t* __restrict__ cnt, BuildCtl* bc) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
          i += (long long)gridDim.x * blockDim.x) {
         const int s = src[i], d = dst[i];
-        unsigned long long a = kSentinel, b = kSentinel;
         if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n) {
-            *bad = 1;
-        } else if (s != d) {
-            a = ((unsigned long long)(unsigned)s << 32) | (unsigned)d;
-            b = ((unsigned long long)(unsigned)d << 32) | (unsigned)s;
+            bc->bad = 1;
+            continue;
         }
-        keys[2 * i] = a;
-        keys[2 * i + 1] = b;
+        if (s == d) continue;
+        atomicAdd(&cnt[s], 1u);
+        atomicAdd(&cnt[d], 1u);
     }
 }
 
-template <typename Off>
-__global__ void k_check_rowptr(const Off* __restrict__ rp, int n, long long nnz, int* bad) {
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
-         u += (long long)gridDim.x * blockDim.x) {
-        if (rp[u + 1] < rp[u]) *bad = 1;
-        if (u == 0 && rp[0] != 0) *bad = 1;
-        if (u == n - 1 && (long long)rp[n] != nnz) *bad = 1;
+__global__ void k_scatter_coo(const int* __restrict__ src, const int* __restrict__ dst, long long S,
+                              int n, const uint32_t* __restrict__ off, uint32_t* __restrict__ fill,
+                              uint32_t* __restrict__ seg) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int s = src[i], d = dst[i];
+        if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n || s == d) continue;
+        seg[off[s] + atomicAdd(&fill[s], 1u)] = (uint32_t)d;
+        seg[off[d] + atomicAdd(&fill[d], 1u)] = (uint32_t)s;
     }
 }
 
+// Raw CSR input: one warp per row; offsets are checked and clamped so that a
+// malformed row_ptr cannot index outside col_idx.
 template <typename Off>
-__global__ void k_expand_csr(const Off* __restrict__ rp, const int* __restrict__ col, int n,
-                             unsigned long long* __restrict__ keys, int* bad) {
+__device__ __forceinline__ bool row_range(const Off* rp, int n, long long nnz, long long u,
+                                          long long* b, long long* e) {
+    const long long lo = (long long)rp[u], hi = (long long)rp[u + 1];
+    bool ok = lo >= 0 && hi >= lo && hi <= nnz;
+    if (u == 0 && lo != 0) ok = false;
+    if (u == n - 1 && hi != nnz) ok = false;
+    *b = ok ? lo : 0;
+    *e = ok ? hi : 0;
+    return ok;
+}
+
+template <typename Off>
+__global__ void k_count_csr(const Off* __restrict__ rp, const int* __restrict__ col, int n,
+                            long long nnz, uint32_t* __restrict__ cnt, BuildCtl* bc) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const long long b = rp[u], e = rp[u + 1];
+        long long b, e;
+        if (!row_range(rp, n, nnz, u, &b, &e)) {
+            if (lane == 0) bc->bad = 1;
+            continue;
+        }
+        unsigned own = 0;
         for (long long j = b + lane; j < e; j += 32) {
             const int v = col[j];
-            unsigned long long x = kSentinel, y = kSentinel;
             if ((unsigned)v >= (unsigned)n) {
-                *bad = 1;
-            } else if (v != (int)u) {
-                x = ((unsigned long long)u << 32) | (unsigned)v;
-                y = ((unsigned long long)(unsigned)v << 32) | (unsigned long long)u;
+                bc->bad = 1;
+                continue;
             }
-            keys[2 * j] = x;
-            keys[2 * j + 1] = y;
+            if (v == (int)u) continue;
+            own++;
+            atomicAdd(&cnt[v], 1u);
+        }
+        own = __reduce_add_sync(kFull, own);
+        if (lane == 0 && own) atomicAdd(&cnt[u], own);
+    }
+}
+
+template <typename Off>
+__global__ void k_scatter_csr(const Off* __restrict__ rp, const int* __restrict__ col, int n,
+                              long long nnz, const uint32_t* __restrict__ off,
+                              uint32_t* __restrict__ fill, uint32_t* __restrict__ seg) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        long long b, e;
+        if (!row_range(rp, n, nnz, u, &b, &e)) continue;
+        for (long long j0 = b; j0 < e; j0 += 32) {
+            const long long j = j0 + lane;
+            int v = -1;
+            if (j < e) v = col[j];
+            const bool ok = j < e && (unsigned)v < (unsigned)n && v != (int)u;
+            const unsigned m = __ballot_sync(kFull, ok);
+            unsigned base = 0;
+            if (lane == 0 && m) base = atomicAdd(&fill[u], (unsigned)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (ok) {
+                seg[off[u] + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)v;
+                seg[off[v] + atomicAdd(&fill[v], 1u)] = (uint32_t)u;
+            }
         }
     }
 }
 
-// ------------------------------------------------------------------ radix sort
+// ------------------------------------------------------------------ segment sorts
+// Bitonic network over P registers (every index is a compile-time constant).
+template <int P>
+__device__ __forceinline__ void sort_regs(uint32_t (&x)[P]) {
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < P; i++) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t a = x[i], b = x[l];
+                    if ((a > b) == up) {
+                        x[i] = b;
+                        x[l] = a;
+                    }
+                }
+            }
+}
+
+template <int P>
+__device__ __forceinline__ uint32_t thread_sort_row(uint32_t* seg, int len) {
+    uint32_t x[P];
+#pragma unroll
+    for (int i = 0; i < P; i++) x[i] = i < len ? seg[i] : kPad;
+    sort_regs<P>(x);
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < P; i++)
+        if (i < len && (i == 0 || x[i] != x[i - 1])) seg[c++] = x[i];
+    return c;
+}
+
+// Rows of at most 32 entries are sorted here; larger ones are listed by class.
+__global__ void k_sort_small(int n, const uint32_t* __restrict__ off, uint32_t* __restrict__ seg,
+                             uint32_t* __restrict__ ucnt, int* __restrict__ mid, int* __restrict__ big,
+                             int* __restrict__ huge, BuildCtl* bc) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x) {
+        const uint32_t o = off[u];
+        const int len = (int)(off[u + 1] - o);
+        uint32_t* s = seg + o;
+        if (len <= 1) {
+            ucnt[u] = (uint32_t)len;
+        } else if (len <= 4) {
+            ucnt[u] = thread_sort_row<4>(s, len);
+        } else if (len <= 8) {
+            ucnt[u] = thread_sort_row<8>(s, len);
+        } else if (len <= 16) {
+            ucnt[u] = thread_sort_row<16>(s, len);
+        } else if (len <= kSmallMax) {
+            ucnt[u] = thread_sort_row<32>(s, len);
+        } else if (len <= kMidMax) {
+            mid[atomicAdd(&bc->n_mid, 1u)] = (int)u;
+        } else if (len <= kBigMax) {
+            big[atomicAdd(&bc->n_big, 1u)] = (int)u;
+        } else {
+            huge[atomicAdd(&bc->n_huge, 1u)] = (int)u;
+            atomicAdd(&bc->huge_entries, (unsigned long long)len);
+        }
+    }
+}
+
+// Warp bitonic sort of 32*E values, blocked layout (lane holds positions
+// lane*E .. lane*E+E-1); partners closer than E are in the same lane.
+template <int E>
+__device__ __forceinline__ void warp_sort(uint32_t (&x)[E]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const int i = lane * E + e;
+                    const bool up = (i & k) == 0;
+                    const uint32_t y = __shfl_xor_sync(kFull, x[e], lj);
+                    const uint32_t lo = min(x[e], y), hi = max(x[e], y);
+                    x[e] = (lower == up) ? lo : hi;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const int l = e ^ j;
+                    if (l > e) {
+                        const int i = lane * E + e;
+                        const bool up = (i & k) == 0;
+                        const uint32_t a = x[e], b = x[l];
+                        if ((a > b) == up) {
+                            x[e] = b;
+                            x[l] = a;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ uint32_t warp_sort_row(uint32_t* seg, int len) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const int i = lane * E + e;
+        x[e] = i < len ? seg[i] : kPad;
+    }
+    warp_sort<E>(x);
+    const uint32_t prev_last = __shfl_up_sync(kFull, x[E - 1], 1);
+    unsigned keep = 0;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const int i = lane * E + e;
+        const uint32_t prev = e == 0 ? prev_last : x[e - 1];
+        if (i < len && (i == 0 || x[e] != prev)) keep |= 1u << e;
+    }
+    const unsigned c = (unsigned)__popc(keep);
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    unsigned pos = incl - c;
+#pragma unroll
+    for (int e = 0; e < E; e++)
+        if ((keep >> e) & 1u) seg[pos++] = x[e];
+    return total;
+}
+
+__global__ void k_sort_mid(const int* __restrict__ mid, const BuildCtl* bc,
+                           const uint32_t* __restrict__ off, uint32_t* __restrict__ seg,
+                           uint32_t* __restrict__ ucnt) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned nm = bc->n_mid;
+    for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; i < nm; i += warps) {
+        const int u = mid[i];
+        const uint32_t o = off[u];
+        const int len = (int)(off[u + 1] - o);
+        uint32_t c;
+        if (len <= 64) c = warp_sort_row<2>(seg + o, len);
+        else if (len <= 128) c = warp_sort_row<4>(seg + o, len);
+        else if (len <= 256) c = warp_sort_row<8>(seg + o, len);
+        else if (len <= 512) c = warp_sort_row<16>(seg + o, len);
+        else c = warp_sort_row<32>(seg + o, len);
+        if (lane == 0) ucnt[u] = c;
+    }
+}
+
+// One CTA per row: bitonic sort in shared memory, then drop repeats.
+__global__ void __launch_bounds__(kBigT) k_sort_big(const int* __restrict__ big, const BuildCtl* bc,
+                                                    const uint32_t* __restrict__ off,
+                                                    uint32_t* __restrict__ seg,
+                                                    uint32_t* __restrict__ ucnt) {
+    extern __shared__ uint32_t sm[];
+    __shared__ unsigned long long wtot;
+    const int tid = threadIdx.x;
+    const unsigned nb = bc->n_big;
+    for (unsigned r = blockIdx.x; r < nb; r += gridDim.x) {
+        const int u = big[r];
+        const uint32_t o = off[u];
+        const int len = (int)(off[u + 1] - o);
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int i = tid; i < P; i += kBigT) sm[i] = i < len ? seg[o + i] : kPad;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = tid; t < P / 2; t += kBigT) {
+                    const int i = 2 * t - (t & (j - 1));
+                    const int l = i + j;
+                    const bool up = (i & k) == 0;
+                    const uint32_t a = sm[i], b = sm[l];
+                    if ((a > b) == up) {
+                        sm[i] = b;
+                        sm[l] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // keep flags over each thread's contiguous chunk, then a block scan
+        const int per = (len + kBigT - 1) / kBigT;
+        const int i0 = min(len, tid * per), i1 = min(len, i0 + per);
+        unsigned c = 0;
+        for (int i = i0; i < i1; i++) c += (i == 0 || sm[i] != sm[i - 1]) ? 1u : 0u;
+        unsigned long long tot;
+        unsigned long long pos = block_excl_scan(c, &tot);
+        for (int i = i0; i < i1; i++)
+            if (i == 0 || sm[i] != sm[i - 1]) seg[o + pos++] = sm[i];
+        if (tid == 0) wtot = tot;
+        __syncthreads();
+        if (tid == 0) ucnt[u] = (uint32_t)wtot;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ hub rows: global radix sort
 constexpr int kRsT = 512, kRsWarps = kRsT / 32, kRsKpt = 8, kRsTile = kRsT * kRsKpt;
 
 __global__ void __launch_bounds__(kRsT) k_rs_hist(const unsigned long long* __restrict__ keys,
@@ -250,29 +522,34 @@ __global__ void __launch_bounds__(kRsT) k_rs_scatter(const unsigned long long* _
         if (dig[r] >= 0) out[(long long)soff[dig[r]] + wc[w][dig[r]] + rank[r]] = key[r];
 }
 
-// Sorts keys[0..N) by the bits vertex ids use; returns the buffer holding the
-// result (keys or alt).
-cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long long N, int idbits,
-                       cudaStream_t st, unsigned long long** result) {
+// Sorts keys[0..N) by bits [0, lowbits) then [32, 32 + highbits) (LSD); returns
+// the buffer holding the result.
+cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long long N, int lowbits,
+                       int highbits, cudaStream_t st, unsigned long long** result) {
     *result = keys;
-    if (N <= 1 || idbits <= 0) return cudaSuccess;
+    if (N <= 1) return cudaSuccess;
     const long long nt = (N + kRsTile - 1) / kRsTile;
     uint32_t *hist = nullptr, *off = nullptr;
     cudaError_t e = cudaMallocAsync(&hist, sizeof(uint32_t) * 256 * nt, st);
     if (e != cudaSuccess) return e;
     e = cudaMallocAsync(&off, sizeof(uint32_t) * 256 * nt, st);
-    if (e != cudaSuccess) { cudaFreeAsync(hist, st); return e; }
+    if (e != cudaSuccess) {
+        cudaFreeAsync(hist, st);
+        return e;
+    }
     std::vector<int> shifts;
-    for (int s = 0; s < idbits; s += 8) shifts.push_back(s);
-    for (int s = 0; s < idbits; s += 8) shifts.push_back(32 + s);
+    for (int s = 0; s < lowbits; s += 8) shifts.push_back(s);
+    for (int s = 0; s < highbits; s += 8) shifts.push_back(32 + s);
     unsigned long long *a = keys, *b = alt;
     for (int sh : shifts) {
         k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(a, N, sh, hist, nt);
+        count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
         e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st);
         if (e != cudaSuccess) break;
         k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(a, b, N, sh, off, nt);
+        count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
         std::swap(a, b);
@@ -283,43 +560,98 @@ cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long l
     return e;
 }
 
-// ------------------------------------------------------------------ dedupe, rows
-struct KeepFlag {
-    const unsigned long long* k;
-    __device__ unsigned long long operator()(long long i) const {
-        const unsigned long long x = k[i];
-        return (x != kSentinel && (i == 0 || k[i - 1] != x)) ? 1ull : 0ull;
+struct HubLen {
+    const int* huge;
+    const uint32_t* off;
+    __device__ unsigned long long operator()(long long r) const {
+        return off[huge[r] + 1] - off[huge[r]];
     }
 };
 
-__global__ void k_compact(const unsigned long long* __restrict__ k, long long N,
-                          const uint32_t* __restrict__ pos, int* __restrict__ col,
-                          uint32_t* __restrict__ rfirst, uint32_t* __restrict__ rlast) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long x = k[i];
-        if (x == kSentinel) continue;
-        const uint32_t u = (uint32_t)(x >> 32);
-        const bool keep = (i == 0 || k[i - 1] != x);
-        if (keep) col[pos[i]] = (int)(uint32_t)(x & 0xffffffffu);
-        if (i == 0 || (uint32_t)(k[i - 1] >> 32) != u) rfirst[u] = pos[i];
-        if (i + 1 == N || (uint32_t)(k[i + 1] >> 32) != u) rlast[u] = pos[i] + (keep ? 1u : 0u);
+// keys of the hub rows: (rank of the row among hub rows) << 32 | column
+__global__ void k_huge_keys(const int* __restrict__ huge, unsigned nh,
+                            const unsigned long long* __restrict__ hoff,
+                            const uint32_t* __restrict__ off, const uint32_t* __restrict__ seg,
+                            unsigned long long* __restrict__ keys) {
+    for (unsigned r = blockIdx.x; r < nh; r += gridDim.x) {
+        const int u = huge[r];
+        const uint32_t o = off[u];
+        const long long len = (long long)(off[u + 1] - o);
+        for (long long i = threadIdx.x; i < len; i += blockDim.x)
+            keys[hoff[r] + i] = ((unsigned long long)r << 32) | seg[o + i];
     }
 }
 
-struct RowDeg {
-    const uint32_t* f;
-    const uint32_t* l;
-    __device__ unsigned long long operator()(long long u) const { return l[u] - f[u]; }
-};
+__global__ void k_huge_back(const int* __restrict__ huge, unsigned nh,
+                            const unsigned long long* __restrict__ hoff,
+                            const uint32_t* __restrict__ off,
+                            const unsigned long long* __restrict__ keys, uint32_t* __restrict__ seg,
+                            uint32_t* __restrict__ ucnt) {
+    __shared__ unsigned long long wtot;
+    for (unsigned r = blockIdx.x; r < nh; r += gridDim.x) {
+        const int u = huge[r];
+        const uint32_t o = off[u];
+        const long long len = (long long)(off[u + 1] - o);
+        const unsigned long long* k = keys + hoff[r];
+        const long long per = (len + blockDim.x - 1) / blockDim.x;
+        const long long i0 = min(len, (long long)threadIdx.x * per), i1 = min(len, i0 + per);
+        unsigned c = 0;
+        for (long long i = i0; i < i1; i++) c += (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
+        unsigned long long tot;
+        unsigned long long pos = block_excl_scan(c, &tot);
+        for (long long i = i0; i < i1; i++)
+            if (i == 0 || k[i] != k[i - 1]) seg[o + pos++] = (uint32_t)(k[i] & 0xffffffffu);
+        if (threadIdx.x == 0) wtot = tot;
+        __syncthreads();
+        if (threadIdx.x == 0) ucnt[u] = (uint32_t)wtot;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ compaction
+// Rows of at most 32 entries: one thread each; the listed larger rows: one warp.
+template <typename Off>
+__global__ void k_compact_small(int n, const uint32_t* __restrict__ off,
+                                const uint32_t* __restrict__ seg, const uint32_t* __restrict__ ucnt,
+                                const Off* __restrict__ rp, int* __restrict__ col) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x) {
+        if (off[u + 1] - off[u] > (uint32_t)kSmallMax) continue;
+        const uint32_t c = ucnt[u];
+        const uint32_t* s = seg + off[u];
+        int* d = col + (long long)rp[u];
+        for (uint32_t i = 0; i < c; i++) d[i] = (int)s[i];
+    }
+}
+
+template <typename Off>
+__global__ void k_compact_list(const int* __restrict__ list, const unsigned* count,
+                               const uint32_t* __restrict__ off, const uint32_t* __restrict__ seg,
+                               const uint32_t* __restrict__ ucnt, const Off* __restrict__ rp,
+                               int* __restrict__ col) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned nl = *count;
+    for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; i < nl; i += warps) {
+        const int u = list[i];
+        const uint32_t c = ucnt[u];
+        const uint32_t* s = seg + off[u];
+        int* d = col + (long long)rp[u];
+        for (uint32_t j = lane; j < c; j += 32) d[j] = (int)s[j];
+    }
+}
 
 template <typename Off>
 __global__ void k_check_clean(const Off* __restrict__ rp, const int* __restrict__ col, int n,
-                              int* bad) {
+                              long long nnz, int* bad) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const long long b = rp[u], e = rp[u + 1];
+        long long b, e;
+        if (!row_range(rp, n, nnz, u, &b, &e)) {
+            if (lane == 0) *bad = 1;
+            continue;
+        }
         for (long long j = b + lane; j < e; j += 32) {
             const int v = col[j];
             if ((unsigned)v >= (unsigned)n || v == (int)u) *bad = 1;
@@ -331,19 +663,22 @@ __global__ void k_check_clean(const Off* __restrict__ rp, const int* __restrict_
 // ------------------------------------------------------------------ tier split
 constexpr int kTsT = 1024;
 
-template <typename Off>
 __device__ __forceinline__ int tier_of(long long d, int t_lo, int t_hi) {
     return d <= t_lo ? 0 : (d <= t_hi ? 1 : 2);
 }
 
 template <typename Off>
 __global__ void __launch_bounds__(kTsT) k_tier_count(const Off* __restrict__ rp, int n, int t_lo,
-                                                     int t_hi, uint32_t* cnt, int nb) {
+                                                     int t_hi, uint32_t* cnt, int nb, int* bad) {
     __shared__ uint32_t c[kTiers];
     if (threadIdx.x < kTiers) c[threadIdx.x] = 0;
     __syncthreads();
     const long long v = (long long)blockIdx.x * kTsT + threadIdx.x;
-    if (v < n) atomicAdd(&c[tier_of<Off>((long long)(rp[v + 1] - rp[v]), t_lo, t_hi)], 1u);
+    if (v < n) {
+        const long long d = (long long)(rp[v + 1] - rp[v]);
+        if (d > (long long)kEstMask) *bad = 1;
+        atomicAdd(&c[tier_of(d, t_lo, t_hi)], 1u);
+    }
     __syncthreads();
     if (threadIdx.x < kTiers) cnt[threadIdx.x * nb + blockIdx.x] = c[threadIdx.x];
 }
@@ -358,7 +693,7 @@ __global__ void __launch_bounds__(kTsT) k_tier_write(const Off* __restrict__ rp,
     const long long v = (long long)blockIdx.x * kTsT + threadIdx.x;
     const bool valid = v < n;
     const long long d = valid ? (long long)(rp[v + 1] - rp[v]) : 0;
-    const int t = valid ? tier_of<Off>(d, t_lo, t_hi) : -1;
+    const int t = valid ? tier_of(d, t_lo, t_hi) : -1;
     unsigned mine = 0;
 #pragma unroll
     for (int q = 0; q < kTiers; q++) {
@@ -370,7 +705,7 @@ __global__ void __launch_bounds__(kTsT) k_tier_write(const Off* __restrict__ rp,
     if (valid) {
         uint32_t before = 0;
         for (int ww = 0; ww < w; ww++) before += wcnt[t][ww];
-        est0[v] = ((uint32_t)t << kEstBits) | (uint32_t)d;
+        est0[v] = ((uint32_t)t << kEstBits) | (uint32_t)(d & kEstMask);
         list[off[t * nb + blockIdx.x] + before + mine] = (int)v;
     }
 }
@@ -397,73 +732,130 @@ struct Temp {
 };
 
 kcore_status cuda_fail(cudaError_t e, const char* what, std::string* err) {
+    cudaGetLastError();
     *err = std::string(what) + ": " + cudaGetErrorString(e);
     return (e == cudaErrorMemoryAllocation) ? KCORE_ERR_OOM : KCORE_ERR_CUDA;
 }
 
-#define KC_TRY(call, what)                                   \
-    do {                                                     \
-        cudaError_t e_ = (call);                             \
+#define KC_TRY(call, what)                                      \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
         if (e_ != cudaSuccess) return cuda_fail(e_, what, err); \
     } while (0)
 
-// keys[0..N) -> clean CSR.
-kcore_status finish_from_keys(Temp& tmp, int64_t n, unsigned long long* keys, long long N,
-                              int off_bytes, cudaStream_t st, DevCsr* out, std::string* err) {
-    unsigned long long* alt = nullptr;
-    KC_TRY(tmp.get(&alt, (size_t)N), "sort buffer");
-    unsigned long long* sorted = keys;
-    KC_TRY(radix_sort(keys, alt, N, id_bits(n), st, &sorted), "radix sort");
-    uint32_t *pos = nullptr, *rfirst = nullptr, *rlast = nullptr;
-    KC_TRY(tmp.get(&pos, (size_t)N + 1), "positions");
-    KC_TRY(exclusive_scan(KeepFlag{sorted}, N, pos, true, st), "dedupe scan");
-    uint32_t total = 0;
-    KC_TRY(cudaMemcpyAsync(&total, pos + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "read size");
+int grid_for(long long items, int per_block) {
+    return (int)std::max<long long>(1, std::min<long long>((items + per_block - 1) / per_block,
+                                                           152LL * 64));
+}
+
+template <typename Off>
+cudaError_t compact(int64_t n, const uint32_t* off, const uint32_t* seg, const uint32_t* ucnt,
+                    const Off* rp, int* col, const int* const lists[3], const unsigned* const counts[3],
+                    const unsigned hc[3], cudaStream_t st) {
+    k_compact_small<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, seg, ucnt, rp, col);
+    count_launch();
+    for (int q = 0; q < 3; q++)
+        if (hc[q]) {
+            k_compact_list<<<grid_for((long long)hc[q] * 32, 256), 256, 0, st>>>(
+                lists[q], counts[q], off, seg, ucnt, rp, col);
+            count_launch();
+        }
+    return cudaGetLastError();
+}
+
+// Steps 2-5, after the counts are in cnt.  `scatter` launches step 3.
+template <typename ScatterFn>
+kcore_status finish(Temp& tmp, int64_t n, uint32_t* cnt, BuildCtl* bc, int off_bytes,
+                    cudaStream_t st, DevCsr* out, std::string* err, ScatterFn scatter) {
+    const long long nn = std::max<int64_t>(n, 1);
+    uint32_t *off = nullptr, *seg = nullptr, *ucnt = nullptr;
+    int *mid = nullptr, *big = nullptr, *huge = nullptr;
+    KC_TRY(tmp.get(&off, (size_t)nn + 1), "row offsets");
+    KC_TRY(exclusive_scan(ReadU32{cnt}, n, off, true, st), "offset scan");
+    uint32_t N = 0;
+    BuildCtl hbc;
+    KC_TRY(cudaMemcpyAsync(&N, off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "read size");
     KC_TRY(cudaStreamSynchronize(st), "sync");
-    if (off_bytes == 4 && total > 0x7fffffffu) {
-        *err = "cleaned graph has 2m >= 2^31 entries; use 8-byte row_ptr";
+    KC_TRY(tmp.get(&seg, (size_t)N), "segments");
+    KC_TRY(tmp.get(&ucnt, (size_t)nn), "distinct counts");
+    KC_TRY(tmp.get(&mid, (size_t)nn), "row lists");
+    KC_TRY(tmp.get(&big, (size_t)std::min<long long>(nn, N / (kMidMax + 1) + 1)), "row lists");
+    KC_TRY(tmp.get(&huge, (size_t)std::min<long long>(nn, N / (kBigMax + 1) + 1)), "row lists");
+    KC_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nn, st), "memset");  // cnt becomes the fill counter
+    KC_TRY(scatter(off, cnt, seg), "scatter");
+    if (n > 0) {
+        k_sort_small<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, seg, ucnt, mid, big, huge, bc);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "sort small rows");
+    }
+    KC_TRY(cudaMemcpyAsync(&hbc, bc, sizeof(BuildCtl), cudaMemcpyDeviceToHost, st), "read classes");
+    KC_TRY(cudaStreamSynchronize(st), "sync");
+    if (hbc.bad) {
+        *err = "an edge endpoint or a row offset is out of range";
         return KCORE_ERR_INVALID;
     }
-    KC_TRY(tmp.get(&rfirst, (size_t)n), "row bounds");
-    KC_TRY(tmp.get(&rlast, (size_t)n), "row bounds");
-    KC_TRY(cudaMemsetAsync(rfirst, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), st), "memset");
-    KC_TRY(cudaMemsetAsync(rlast, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), st), "memset");
-    kcore_status s = dmalloc((void**)&out->col, sizeof(int) * std::max<size_t>(total, 1), err);
-    if (s != KCORE_OK) return s;
-    s = dmalloc(&out->row_ptr, (size_t)off_bytes * (n + 1), err);
-    if (s != KCORE_OK) return s;
-    if (N > 0) {
-        const int g = (int)std::min<long long>((N + 255) / 256, 152LL * 64);
-        k_compact<<<g, 256, 0, st>>>(sorted, N, pos, out->col, rfirst, rlast);
-        KC_TRY(cudaGetLastError(), "compact");
+    if (hbc.n_mid) {
+        k_sort_mid<<<grid_for((long long)hbc.n_mid * 32, 256), 256, 0, st>>>(mid, bc, off, seg, ucnt);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "sort mid rows");
     }
+    if (hbc.n_big) {
+        const size_t smem = sizeof(uint32_t) * kBigMax;
+        KC_TRY(cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem), "smem attribute");
+        k_sort_big<<<(unsigned)std::min<unsigned>(hbc.n_big, 152u * 2u), kBigT, smem, st>>>(
+            big, bc, off, seg, ucnt);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "sort big rows");
+    }
+    if (hbc.n_huge) {
+        const long long H = (long long)hbc.huge_entries;
+        unsigned long long *keys = nullptr, *alt = nullptr, *hoff = nullptr, *sorted = nullptr;
+        KC_TRY(tmp.get(&keys, (size_t)H), "hub keys");
+        KC_TRY(tmp.get(&alt, (size_t)H), "hub keys");
+        KC_TRY(tmp.get(&hoff, (size_t)hbc.n_huge + 1), "hub offsets");
+        KC_TRY(exclusive_scan(HubLen{huge, off}, (long long)hbc.n_huge, hoff, true, st), "hub offsets");
+        const unsigned g = std::min<unsigned>(hbc.n_huge, 152u * 4u);
+        k_huge_keys<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, seg, keys);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "hub keys");
+        KC_TRY(radix_sort(keys, alt, H, id_bits(n), id_bits(hbc.n_huge), st, &sorted), "hub sort");
+        k_huge_back<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, sorted, seg, ucnt);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "hub write back");
+    }
+    // row_ptr and col_idx (col sized by the entries before repeats were dropped)
+    kcore_status s = dmalloc(&out->row_ptr, (size_t)off_bytes * (n + 1), err, st);
+    if (s != KCORE_OK) return s;
+    s = dmalloc((void**)&out->col, sizeof(int) * std::max<size_t>(N, 1), err, st);
+    if (s != KCORE_OK) return s;
     if (off_bytes == 8)
-        KC_TRY(exclusive_scan(RowDeg{rfirst, rlast}, n, (long long*)out->row_ptr, true, st), "row scan");
+        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (long long*)out->row_ptr, true, st), "row scan");
     else
-        KC_TRY(exclusive_scan(RowDeg{rfirst, rlast}, n, (int*)out->row_ptr, true, st), "row scan");
+        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (int*)out->row_ptr, true, st), "row scan");
+    if (n > 0) {
+        const int* const lists[3] = {mid, big, huge};
+        const unsigned* const counts[3] = {&bc->n_mid, &bc->n_big, &bc->n_huge};
+        const unsigned hc[3] = {hbc.n_mid, hbc.n_big, hbc.n_huge};
+        if (off_bytes == 8)
+            KC_TRY(compact(n, off, seg, ucnt, (const long long*)out->row_ptr, out->col, lists, counts,
+                           hc, st), "compact");
+        else
+            KC_TRY(compact(n, off, seg, ucnt, (const int*)out->row_ptr, out->col, lists, counts, hc,
+                           st), "compact");
+    }
+    long long nnz = 0;
+    KC_TRY(cudaMemcpyAsync(&nnz, (const char*)out->row_ptr + (size_t)off_bytes * n, off_bytes,
+                           cudaMemcpyDeviceToHost, st), "read nnz");
     KC_TRY(cudaStreamSynchronize(st), "sync");
+    if (off_bytes == 4) nnz = (long long)(int32_t)(nnz & 0xffffffffLL);
     out->n = n;
-    out->nnz = total;
+    out->nnz = nnz;
     out->off_bytes = off_bytes;
     return KCORE_OK;
 }
 
 }  // namespace
-
-kcore_status dmalloc(void** p, size_t bytes, std::string* err) {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        *err = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? KCORE_ERR_OOM : KCORE_ERR_CUDA;
-    }
-    return KCORE_OK;
-}
-
-void dfree(void* p) {
-    if (p) cudaFree(p);
-}
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,
                             cudaStream_t st) {
@@ -477,25 +869,30 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
         return KCORE_ERR_INVALID;
     }
     Temp tmp(st);
-    const long long N = 2 * (long long)samples;
-    unsigned long long* keys = nullptr;
-    int* bad = nullptr;
-    KC_TRY(tmp.get(&keys, (size_t)N), "key buffer");
-    KC_TRY(tmp.get(&bad, 1), "flag");
-    KC_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
+    uint32_t* cnt = nullptr;
+    BuildCtl* bc = nullptr;
+    KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
+    KC_TRY(tmp.get(&bc, 1), "build state");
+    KC_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), st), "memset");
+    KC_TRY(cudaMemsetAsync(bc, 0, sizeof(BuildCtl), st), "memset");
     if (samples > 0) {
-        const int g = (int)std::min<long long>((samples + 255) / 256, 152LL * 64);
-        k_expand_coo<<<g, 256, 0, st>>>(src, dst, samples, (int)n, keys, bad);
-        KC_TRY(cudaGetLastError(), "expand");
+        k_count_coo<<<grid_for(samples, 256), 256, 0, st>>>(src, dst, samples, (int)n, cnt, bc);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "count");
     }
-    int hbad = 0;
-    KC_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
-    if (hbad) {
-        *err = "edge endpoint outside [0, n)";
+    kcore_status s = finish(tmp, n, cnt, bc, off_bytes, st, out, err,
+                            [&](const uint32_t* off, uint32_t* fill, uint32_t* seg) {
+                                if (samples == 0) return cudaSuccess;
+                                k_scatter_coo<<<grid_for(samples, 256), 256, 0, st>>>(
+                                    src, dst, samples, (int)n, off, fill, seg);
+                                count_launch();
+                                return cudaGetLastError();
+                            });
+    if (s == KCORE_OK && off_bytes == 4 && out->nnz > 0x7fffffffLL) {
+        *err = "cleaned graph has 2m >= 2^31 entries; use 8-byte row_ptr";
         return KCORE_ERR_INVALID;
     }
-    return finish_from_keys(tmp, n, keys, N, off_bytes, st, out, err);
+    return s;
 }
 
 kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, const int* col,
@@ -506,41 +903,38 @@ kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, co
         return KCORE_ERR_INVALID;
     }
     Temp tmp(st);
-    int* bad = nullptr;
-    KC_TRY(tmp.get(&bad, 1), "flag");
-    KC_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
-    const int g = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 64));
+    uint32_t* cnt = nullptr;
+    BuildCtl* bc = nullptr;
+    KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
+    KC_TRY(tmp.get(&bc, 1), "build state");
+    KC_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), st), "memset");
+    KC_TRY(cudaMemsetAsync(bc, 0, sizeof(BuildCtl), st), "memset");
+    const int g = grid_for(n * 32, 256);
     if (n > 0) {
         if (in_off_bytes == 8)
-            k_check_rowptr<<<g, 256, 0, st>>>((const long long*)row_ptr, (int)n, nnz, bad);
+            k_count_csr<<<g, 256, 0, st>>>((const long long*)row_ptr, col, (int)n, nnz, cnt, bc);
         else
-            k_check_rowptr<<<g, 256, 0, st>>>((const int*)row_ptr, (int)n, nnz, bad);
-        KC_TRY(cudaGetLastError(), "check row_ptr");
+            k_count_csr<<<g, 256, 0, st>>>((const int*)row_ptr, col, (int)n, nnz, cnt, bc);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "count");
     }
-    int hbad = 0;
-    KC_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
-    if (hbad) {
-        *err = "row_ptr must start at 0, be non-decreasing and end at nnz";
+    kcore_status s = finish(tmp, n, cnt, bc, off_bytes, st, out, err,
+                            [&](const uint32_t* off, uint32_t* fill, uint32_t* seg) {
+                                if (n == 0) return cudaSuccess;
+                                if (in_off_bytes == 8)
+                                    k_scatter_csr<<<g, 256, 0, st>>>((const long long*)row_ptr, col,
+                                                                     (int)n, nnz, off, fill, seg);
+                                else
+                                    k_scatter_csr<<<g, 256, 0, st>>>((const int*)row_ptr, col, (int)n,
+                                                                     nnz, off, fill, seg);
+                                count_launch();
+                                return cudaGetLastError();
+                            });
+    if (s == KCORE_OK && off_bytes == 4 && out->nnz > 0x7fffffffLL) {
+        *err = "cleaned graph has 2m >= 2^31 entries; use 8-byte row_ptr";
         return KCORE_ERR_INVALID;
     }
-    const long long N = 2 * (long long)nnz;
-    unsigned long long* keys = nullptr;
-    KC_TRY(tmp.get(&keys, (size_t)N), "key buffer");
-    if (n > 0 && nnz > 0) {
-        if (in_off_bytes == 8)
-            k_expand_csr<<<g, 256, 0, st>>>((const long long*)row_ptr, col, (int)n, keys, bad);
-        else
-            k_expand_csr<<<g, 256, 0, st>>>((const int*)row_ptr, col, (int)n, keys, bad);
-        KC_TRY(cudaGetLastError(), "expand");
-    }
-    KC_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
-    if (hbad) {
-        *err = "col_idx entry outside [0, n)";
-        return KCORE_ERR_INVALID;
-    }
-    return finish_from_keys(tmp, n, keys, N, off_bytes, st, out, err);
+    return s;
 }
 
 kcore_status check_clean_csr(int64_t n, const void* row_ptr, int off_bytes, const int* col,
@@ -549,22 +943,20 @@ kcore_status check_clean_csr(int64_t n, const void* row_ptr, int off_bytes, cons
     int* bad = nullptr;
     KC_TRY(tmp.get(&bad, 1), "flag");
     KC_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
-    const int g = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 64));
     if (n > 0) {
-        if (off_bytes == 8) {
-            k_check_rowptr<<<g, 256, 0, st>>>((const long long*)row_ptr, (int)n, nnz, bad);
-            k_check_clean<<<g, 256, 0, st>>>((const long long*)row_ptr, col, (int)n, bad);
-        } else {
-            k_check_rowptr<<<g, 256, 0, st>>>((const int*)row_ptr, (int)n, nnz, bad);
-            k_check_clean<<<g, 256, 0, st>>>((const int*)row_ptr, col, (int)n, bad);
-        }
+        const int g = grid_for(n * 32, 256);
+        if (off_bytes == 8)
+            k_check_clean<<<g, 256, 0, st>>>((const long long*)row_ptr, col, (int)n, nnz, bad);
+        else
+            k_check_clean<<<g, 256, 0, st>>>((const int*)row_ptr, col, (int)n, nnz, bad);
+        count_launch();
         KC_TRY(cudaGetLastError(), "check");
     }
     int hbad = 0;
     KC_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
     KC_TRY(cudaStreamSynchronize(st), "sync");
     if (hbad) {
-        *err = "KCORE_IN_CLEAN graph has an unsorted row, a repeat, a self-loop or a bad id";
+        *err = "KCORE_IN_CLEAN graph has a bad offset, an unsorted row, a repeat, a self-loop or a bad id";
         return KCORE_ERR_INVALID;
     }
     return KCORE_OK;
@@ -578,12 +970,16 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
     Temp tmp(st);
     const int nb = (int)((n + kTsT - 1) / kTsT);
     uint32_t *cnt = nullptr, *off = nullptr;
+    int* bad = nullptr;
     KC_TRY(tmp.get(&cnt, (size_t)kTiers * nb), "tier counts");
     KC_TRY(tmp.get(&off, (size_t)kTiers * nb + 1), "tier offsets");
+    KC_TRY(tmp.get(&bad, 1), "flag");
+    KC_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
     if (off_bytes == 8)
-        k_tier_count<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, cnt, nb);
+        k_tier_count<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, bad);
     else
-        k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb);
+        k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, bad);
+    count_launch();
     KC_TRY(cudaGetLastError(), "tier count");
     KC_TRY(exclusive_scan(ReadU32{cnt}, (long long)kTiers * nb, off, true, st), "tier scan");
     if (off_bytes == 8)
@@ -592,14 +988,19 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
     else
         k_tier_write<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, off, nb, est0,
                                           init_list);
+    count_launch();
     KC_TRY(cudaGetLastError(), "tier write");
-    std::vector<uint32_t> h(kTiers + 1);
-    for (int q = 0; q <= kTiers; q++) {
-        const long long idx = (q < kTiers) ? (long long)q * nb : (long long)kTiers * nb;
-        KC_TRY(cudaMemcpyAsync(&h[q], off + idx, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
-               "read tier offsets");
-    }
+    uint32_t h[kTiers + 1];
+    int hbad = 0;
+    for (int q = 0; q <= kTiers; q++)
+        KC_TRY(cudaMemcpyAsync(&h[q], off + (long long)q * nb, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, st), "read tier offsets");
+    KC_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
     KC_TRY(cudaStreamSynchronize(st), "sync");
+    if (hbad) {
+        *err = "a vertex degree is 2^30 or more";
+        return KCORE_ERR_INVALID;
+    }
     for (int q = 0; q < kTiers; q++) tier_cnt[q] = (long long)h[q + 1] - h[q];
     return KCORE_OK;
 }

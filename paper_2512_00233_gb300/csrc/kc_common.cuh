@@ -17,15 +17,17 @@ namespace kc {
 constexpr uint32_t kEstBits = 30;
 constexpr uint32_t kEstMask = (1u << kEstBits) - 1u;
 constexpr int kTiers = 3;
-constexpr int kSlots = 3;        // rotating per-sweep counter slots
 constexpr int kHubBins = 4096;   // shared-memory histogram of the CTA tier
 
 // Accumulator indices of per-sweep statistics.
 enum { kAccEvaluated = 0, kAccDegsum = 1, kAccUpdates = 2, kAccPushes = 3, kAccN = 4 };
 
-// Control block of the persistent sweep kernel (device memory).  Slot s % 3
-// holds the frontier counts of sweep s; sweep s pushes into slot (s+1) % 3 and
-// the slot of sweep s-1 is cleared at the start of sweep s.
+// Control block of the persistent sweep kernel (device memory).  Counter slot
+// s % 4 holds the frontier counts of sweep s; sweep s pushes into slot
+// (s+1) % 4, reads the size of F_{s-1} from slot (s-1) % 4 to clear its
+// membership bits, and slot (s+2) % 4 is reset at the start of sweep s.
+constexpr int kSlots = 4;
+constexpr int kParities = 3;     // frontier lists / membership bitmaps
 struct SweepCtl {
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int bar_gen;            // grid barrier generation
@@ -36,7 +38,6 @@ struct SweepCtl {
     unsigned int fcnt[kSlots][4];    // frontier size per tier
     unsigned int cursor[kSlots][4];  // work cursor per tier
     unsigned int ucnt[kSlots];       // synchronous mode: updates this sweep
-    unsigned int pad0;
     unsigned long long acc[kSlots][kAccN];
     unsigned long long tot[kAccN];
     unsigned int tail_epoch;         // bumped when the single-CTA tail hands over
@@ -44,24 +45,26 @@ struct SweepCtl {
     long long resume_sweep;
 };
 
-// Arguments of one persistent sweep launch.
+// Arguments of one persistent sweep launch.  Sweep s reads frontier list and
+// membership bitmap s % 3, pushes into (s+1) % 3 and clears (s+2) % 3.
 struct SweepArgs {
     const void* row_ptr;             // int32 or int64 per off64
     const int* col;
     uint32_t* est;
     const int* init_list;            // frontier of sweep 0 (tiers contiguous), or null
-    int* list[2];                    // frontier lists by sweep parity
-    uint32_t* bitmap[2];             // frontier membership by sweep parity
+    int* list[kParities];            // frontier lists
+    uint32_t* bitmap[kParities];     // frontier membership
     int* upd_list;                   // synchronous mode: updated vertices
     int* upd_val;                    // synchronous mode: their new (then old) values
     long long tier_off[kTiers];      // start of each tier inside a list
     SweepCtl* ctl;
-    long long* trace;                // [max_trace][3]: frontier, degsum, updates
+    long long* trace;                // [max_trace][4]: frontier, degsum, updates, start ns
     long long max_trace;
     long long first_sweep;           // sweep index at which this launch starts
     long long max_sweeps;            // NOT_CONVERGED at this sweep index
     long long stop_sweep;            // this launch ends before this sweep index
     long long timeout_ns;            // budget of every bounded wait
+    long long words;                 // 32-bit words per bitmap
     int n;
     int t_lo, t_hi;
     int low_chunk, med_chunk;
@@ -109,8 +112,16 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
 cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,
                             cudaStream_t st);
 
-// Device allocation helpers (report OOM separately from other CUDA errors).
-kcore_status dmalloc(void** p, size_t bytes, std::string* err);
-void dfree(void* p);
+// Number of kernels this library has launched in the process (all devices).
+void count_launch();
+long long launches();
+
+// Device memory from the library's stream-ordered pool (OOM reported apart
+// from other CUDA errors), and recycled small pinned host blocks.
+kcore_status dmalloc(void** p, size_t bytes, std::string* err, cudaStream_t st = 0);
+void dfree(void* p, cudaStream_t st = 0);
+constexpr size_t kPinnedBlock = 4096;
+cudaError_t pinned_get(void** p, size_t bytes);
+void pinned_put(void* p);
 
 }  // namespace kc

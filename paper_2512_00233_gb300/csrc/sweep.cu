@@ -3,20 +3,32 @@
 // One cooperative launch runs every sweep.  Sweep s evaluates the vertices of
 // frontier F_s: each computes the h-index of its neighbours' estimates capped
 // at its own estimate (computeCoreness of Alg. 1, read as Montresor's
-// computeIndex).  If that is lower, the estimate is lowered and every
-// neighbour v whose estimate is above the new value is pushed into F_{s+1}
-// (selective sending, Sec. III-B).  Estimates only decrease, so they are
-// updated in place while other vertices of the same sweep read them
-// (asynchronous mode); a stale read only over-activates, never misses a needed
-// re-evaluation.  The run ends when a frontier is empty (the `changed` flag of
-// Alg. 2/3 becomes the frontier count).
+// computeIndex).  If that is lower, the estimate is lowered and neighbours are
+// pushed into F_{s+1} by the activation rule (below).  Estimates only
+// decrease, so they are updated in place while other vertices of the same
+// sweep read them (asynchronous mode).  The run ends when a frontier is empty
+// (the `changed` flag of Alg. 2/3 becomes the frontier count).
 //
-// Degree tiers (est word bits 30-31): d <= t_lo one thread per vertex with a
-// register histogram; d <= t_hi one warp per vertex, counts by warp reduction;
-// larger degrees one CTA per vertex with a shared-memory histogram.  Work is
-// handed out by atomic cursors (the dynamic chunking of Alg. 2), hubs first.
-// Frontier membership is a bitmap per sweep parity (no vertex twice in a
-// list); pushes are warp-aggregated.
+// Activation (u lowered from k to h, x = the value of est[v] that u reads):
+//   simple  (selective sending, Sec. III-B):          push v iff h < x.
+//   refined (Sec. IV, Further Optimizations):         push v iff h < x and
+//           (x <= k  or  v is in F_s).
+// Only v writes est[v], and only while it is evaluated, so for v outside F_s
+// the value u reads is exact and FastK's condition x <= old_u applies as is;
+// for v inside F_s the read may be stale and the simple rule is used.  Either
+// way every vertex whose support u withdraws is re-evaluated; a stale read can
+// only over-activate.  (The plain refined condition without the F_s clause is
+// unsafe with in-place updates: v may lower concurrently using u's old value.)
+//
+// Degree tiers (est word bits 30-31): d <= t_lo one thread per vertex, its
+// neighbour ids and estimates in registers and a byte-packed register
+// histogram; d <= t_hi one warp per vertex, counts by warp reduction; larger
+// degrees one CTA per vertex with a shared-memory histogram.  Work is handed
+// out by atomic cursors (the dynamic chunking of Alg. 2), hubs first.
+// Frontier membership is a bitmap per sweep (no vertex twice in a list);
+// pushes are warp-aggregated.  Lists and bitmaps rotate over three sweeps so
+// that F_s membership stays readable during sweep s and F_{s-1}'s bits are
+// cleared during sweep s.
 //
 // Sweeps are separated by a grid barrier; once a frontier is at most tail_max
 // vertices, CTA 0 continues alone with block barriers (the GPU analogue of
@@ -26,9 +38,8 @@
 //
 // Synchronous mode (KCORE_SYNC_MODE) follows Alg. 3: phase A computes new
 // values against the unchanged estimates and records them; after a barrier
-// phase B writes them; with the refined rule (Sec. IV, Further
-// Optimizations) a third phase decides activations against the written
-// values: new_u < est(v) <= old_u.
+// phase B writes them; with the refined rule a third phase decides
+// activations against the written values: new_u < est(v) <= old_u.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +52,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlock = 512;
+constexpr int kMinBlocks = 2;
+constexpr int kMedR = 8;             // warp tier: up to 32 * kMedR neighbours
 
 __device__ __forceinline__ unsigned long long gtime_ns() {
     unsigned long long t;
@@ -55,43 +68,159 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long* p)
     return *(const volatile unsigned long long*)p;
 }
 
-// Estimates are read through L2 (ld.global.cg): another SM may have lowered
-// them, and an L1 copy from an earlier sweep would be stale.
+// Estimates, lists and bitmaps are read through L2 (ld.global.cg): another SM
+// may have written them, and an L1 copy from an earlier sweep would be stale.
 __device__ __forceinline__ uint32_t est_load(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ int list_load(const int* p) { return __ldcg(p); }
 
-struct Sweep {
-    const SweepArgs* a;
-    int cur, nxt;
-    const int* lcur;
-    int* lnxt;
-    uint32_t* bmc;
-    uint32_t* bmn;
+struct Acc {
+    unsigned long long evaluated, degsum, updates, pushes;
 };
 
-// All 32 lanes call this.  A lane with `want` pushes v (tier `tier`) into the
-// next frontier unless it is already there.
-__device__ __forceinline__ void warp_push(const Sweep& S, bool want, int v, uint32_t tier,
-                                          unsigned long long& pushes) {
+// Per-warp push buffers: each warp collects its pushes in its own slice of
+// shared memory and appends them to the global frontier list itself, with one
+// atomic per tier per flush (a single global counter per tier would otherwise
+// serialise every push) and coalesced stores.  No CTA-wide synchronisation.
+constexpr int kWCap0 = 64, kWCap1 = 32, kWCap2 = 32;
+constexpr int kWCap = kWCap0 + kWCap1 + kWCap2;
+
+__device__ __forceinline__ int wcap(int q) { return q == 0 ? kWCap0 : (q == 1 ? kWCap1 : kWCap2); }
+__device__ __forceinline__ int woff(int q) { return q == 0 ? 0 : (q == 1 ? kWCap0 : kWCap0 + kWCap1); }
+
+struct Sweep {
+    const SweepArgs* a;
+    int cur, nxt;          // counter slots
+    const int* lcur;
+    int* lnxt;
+    const uint32_t* bmc;   // F_s membership
+    uint32_t* bmn;         // F_{s+1} membership
+    int* wbuf;             // shared: this warp's push buffer (kWCap entries)
+};
+
+// Warp-uniform fill counts of the warp's push buffer.
+struct WarpQ {
+    unsigned n[kTiers];
+};
+
+__device__ __forceinline__ bool in_current(const Sweep& S, int v) {
+    return (__ldcg(S.bmc + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Activation rule for a neighbour v read as x while u goes from k to h.
+__device__ __forceinline__ bool should_push(const Sweep& S, int h, int k, int x, int v) {
+    if (x <= h) return false;
+    if (!S.a->refined || x <= k) return true;
+    return in_current(S, v);
+}
+
+// Appends the warp's buffered pushes of tier q to the global list.  All 32
+// lanes call (warp-uniform).
+__device__ __forceinline__ void warp_flush(const Sweep& S, WarpQ& Q, int q) {
+    const unsigned c = Q.n[q];
+    if (c == 0) return;
     const int lane = threadIdx.x & 31;
-    bool fresh = false;
-    if (want) {
-        const uint32_t bit = 1u << (v & 31);
-        uint32_t* word = S.bmn + (v >> 5);
-        if ((__ldcg(word) & bit) == 0) fresh = (atomicOr(word, bit) & bit) == 0;
-    }
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&S.a->ctl->fcnt[S.nxt][q], c);
+    base = __shfl_sync(kFull, base, 0);
+    int* dst = S.lnxt + S.a->tier_off[q] + base;
+    for (unsigned i = lane; i < c; i += 32) dst[i] = S.wbuf[woff(q) + i];
+    __syncwarp();
+    Q.n[q] = 0;
+}
+
+__device__ __forceinline__ void warp_flush_all(const Sweep& S, WarpQ& Q) {
+#pragma unroll
+    for (int q = 0; q < kTiers; q++) warp_flush(S, Q, q);
+}
+
+// All 32 lanes call this.  A lane with `fresh` appends v (tier `tier`) to
+// the warp's push buffer; v's membership bit is already claimed.
+__device__ __forceinline__ void warp_enqueue(const Sweep& S, WarpQ& Q, bool fresh, int v,
+                                             uint32_t tier, Acc& acc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned any = __ballot_sync(kFull, fresh);
+    if (!any) return;
 #pragma unroll
     for (int q = 0; q < kTiers; q++) {
         const unsigned m = __ballot_sync(kFull, fresh && tier == (uint32_t)q);
         if (m) {
-            const int leader = __ffs(m) - 1;
-            unsigned base = 0;
-            if (lane == leader) base = atomicAdd(&S.a->ctl->fcnt[S.nxt][q], (unsigned)__popc(m));
-            base = __shfl_sync(kFull, base, leader);
+            const unsigned cnt = (unsigned)__popc(m);
+            if (Q.n[q] + cnt > (unsigned)wcap(q)) warp_flush(S, Q, q);
             if (fresh && tier == (uint32_t)q)
-                S.lnxt[S.a->tier_off[q] + base + __popc(m & ((1u << lane) - 1u))] = v;
-            if (lane == 0) pushes += (unsigned)__popc(m);
+                S.wbuf[woff(q) + Q.n[q] + __popc(m & ((1u << lane) - 1u))] = v;
+            Q.n[q] += cnt;
+            __syncwarp();
         }
+    }
+    if (lane == 0) acc.pushes += (unsigned)__popc(any);
+}
+
+// Claims v's bit in the next frontier's bitmap; true if this call set it.
+__device__ __forceinline__ bool claim(const Sweep& S, int v) {
+    const uint32_t bit = 1u << (v & 31);
+    uint32_t* word = S.bmn + (v >> 5);
+    if (__ldcg(word) & bit) return false;
+    return (atomicOr(word, bit) & bit) == 0;
+}
+
+// All 32 lanes call this: claim and enqueue one candidate per lane.
+__device__ __forceinline__ void warp_push(const Sweep& S, WarpQ& Q, bool want, int v,
+                                          uint32_t tier, Acc& acc) {
+    const bool fresh = want && claim(S, v);
+    warp_enqueue(S, Q, fresh, v, tier, acc);
+}
+
+// Pushes up to N candidates per lane (bit j of `cand` selects vs[j]).  The
+// activation filter, the bitmap pre-tests and the atomics of all N slots are
+// issued before any result is used, so they overlap in flight.  All lanes call.
+template <int N>
+__device__ __forceinline__ void warp_push_n(const Sweep& S, WarpQ& Q, uint32_t cand, int h, int k,
+                                            const int (&vs)[N], const uint32_t (&xw)[N],
+                                            Acc& acc) {
+    if (!__any_sync(kFull, cand != 0)) return;
+    uint32_t word[N];
+    if (S.a->refined) {
+        // refined rule: a candidate read above k is kept only if it is in F_s
+#pragma unroll
+        for (int j = 0; j < N; j++)
+            word[j] = ((cand >> j) & 1u) && (int)(xw[j] & kEstMask) > k
+                          ? __ldcg(S.bmc + (vs[j] >> 5)) : 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < N; j++)
+            if (((cand >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) cand &= ~(1u << j);
+    }
+#pragma unroll
+    for (int j = 0; j < N; j++)
+        word[j] = ((cand >> j) & 1u) ? __ldcg(S.bmn + (vs[j] >> 5)) : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        const uint32_t bit = 1u << (vs[j] & 31);
+        if (((cand >> j) & 1u) && !(word[j] & bit)) word[j] = atomicOr(S.bmn + (vs[j] >> 5), bit);
+        else word[j] = 0xffffffffu;
+    }
+    uint32_t fresh = 0;
+#pragma unroll
+    for (int j = 0; j < N; j++)
+        if (((cand >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) fresh |= 1u << j;
+    if (!__any_sync(kFull, fresh != 0)) return;
+#pragma unroll
+    for (int j = 0; j < N; j++)
+        if (__any_sync(kFull, (fresh >> j) & 1u))
+            warp_enqueue(S, Q, (fresh >> j) & 1u, vs[j], xw[j] >> kEstBits, acc);
+}
+
+// Hands out items [0, count) of one tier: each warp takes `warp_items` at a
+// time from the global cursor and calls fn(lo, hi).
+template <class Fn>
+__device__ __forceinline__ void run_tier(unsigned* cursor, unsigned count, unsigned warp_items,
+                                         Fn fn) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(cursor, warp_items);
+        i = __shfl_sync(kFull, i, 0);
+        if (i >= count) return;
+        fn(i, min(count, i + warp_items));
     }
 }
 
@@ -118,81 +247,189 @@ __device__ __forceinline__ void warp_update(const Sweep& S, bool changed, int u,
     }
 }
 
-__device__ __forceinline__ void clear_member(const Sweep& S, int u) {
-    atomicAnd(S.bmc + (u >> 5), ~(1u << (u & 31)));
+// ---------------------------------------------------------------- thread tier
+// Edge-parallel evaluation of 32 low-degree vertices, one per lane.  The warp
+// takes an exclusive prefix sum of their degrees and walks their combined
+// adjacency one entry per lane per step; the owner of entry g is the last lane
+// whose prefix is <= g (a five-step shuffle bisection).  Each entry adds
+// min(x, k_owner) to its owner's histogram of threshold counts, held in shared
+// memory as bytes: word i of lane o counts #{x >= t} for t = 4i+1 .. 4i+4.
+// The capped h-index of the owner is the number of thresholds t with
+// count_t >= t, because that predicate holds exactly for t <= h.
+// The first kLowCache steps keep their (entry, estimate) pairs in registers
+// for the activation pass; longer walks read them again.
+constexpr int kLowCache = 4;
+
+__device__ __forceinline__ uint32_t byte_ramp(int q) {
+    // bytes 0..q-1 set to 1 (q clamped to [0, 4])
+    return q >= 4 ? 0x01010101u : (q <= 0 ? 0u : (0x01010101u & ((1u << (8 * q)) - 1u)));
 }
 
-// ---------------------------------------------------------------- thread tier
-// Register histogram: c[i] packs the counts #{x >= t} for the four thresholds
-// t = 4i+1 .. 4i+4, one byte each (x = min(neighbour estimate, k)).  The
-// capped h-index is the number of thresholds t with count_t >= t, because that
-// predicate holds exactly for t <= h.
-template <typename Off, int TW>
-__device__ __forceinline__ void low_vertex(const Sweep& S, const Off* __restrict__ rp, bool valid,
-                                           int u, unsigned long long acc[kAccN]) {
+__device__ __forceinline__ int owner_of(int g, int excl) {
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int e = __shfl_sync(kFull, excl, o + step);
+        if (e <= g) o += step;
+    }
+    return o;
+}
+
+template <typename Off, int TW, bool DENSE>
+__device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
+                                         bool valid, int u, uint32_t* hist, Acc& acc) {
     const SweepArgs& a = *S.a;
+    const int lane = threadIdx.x & 31;
     long long b = 0;
     int d = 0, k = 0;
     uint32_t w = 0;
     if (valid) {
+        w = est_load(a.est + u);
         b = (long long)rp[u];
         d = (int)((long long)rp[u + 1] - b);
-        w = est_load(a.est + u);
         k = (int)(w & kEstMask);
-        clear_member(S, u);
-        acc[kAccEvaluated] += 1;
-        acc[kAccDegsum] += (unsigned)d;
+    }
+    if (DENSE) valid = valid && (w >> kEstBits) == 0;  // the other tiers run from their lists
+    if (valid) {
+        acc.evaluated += 1;
+        acc.degsum += (unsigned)d;
     }
     const bool work = valid && k > 0;
-    uint32_t c[TW];
+    const int dd = work ? d : 0;
+    int incl = dd;
 #pragma unroll
-    for (int i = 0; i < TW; i++) c[i] = 0;
-    const int dmax = __reduce_max_sync(kFull, work ? d : 0);
-    for (int j = 0; j < dmax; j++) {
-        if (work && j < d) {
-            const int v = __ldg(a.col + b + j);
-            const int x = (int)(est_load(a.est + v) & kEstMask);
-            const int y = x < k ? x : k;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - dd;
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+#pragma unroll
+    for (int i = 0; i < TW; i++) hist[i * 32 + lane] = 0;
+    __syncwarp();
+    // pass 1: histograms.  The first kLowCache steps issue all their loads
+    // before using any (two dependent round trips in all); longer walks loop.
+    int cv[kLowCache], co[kLowCache];
+    uint32_t cx[kLowCache];
+#pragma unroll
+    for (int c = 0; c < kLowCache; c++) {
+        const int g = 32 * c + lane;
+        co[c] = owner_of(g, excl);
+        const long long bo = __shfl_sync(kFull, b, co[c]);
+        const int eo = __shfl_sync(kFull, excl, co[c]);
+        cv[c] = g < total ? __ldg(a.col + bo + (g - eo)) : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < kLowCache; c++) cx[c] = cv[c] >= 0 ? est_load(a.est + cv[c]) : 0u;
+#pragma unroll
+    for (int c = 0; c < kLowCache; c++) {
+        const int ko = __shfl_sync(kFull, k, co[c]);
+        if (cv[c] >= 0) {
+            const int x = (int)(cx[c] & kEstMask);
+            const int y = x < ko ? x : ko;
 #pragma unroll
             for (int i = 0; i < TW; i++) {
-                const int q = y - 4 * i;
-                c[i] += q >= 4 ? 0x01010101u : (q <= 0 ? 0u : (0x01010101u & ((1u << (8 * q)) - 1u)));
+                const uint32_t m = byte_ramp(y - 4 * i);
+                if (m) atomicAdd(&hist[i * 32 + co[c]], m);
             }
         }
     }
+    for (int g0 = 32 * kLowCache; g0 < total; g0 += 32) {
+        const int g = g0 + lane;
+        const int o = owner_of(g, excl);
+        const long long bo = __shfl_sync(kFull, b, o);
+        const int eo = __shfl_sync(kFull, excl, o);
+        const int ko = __shfl_sync(kFull, k, o);
+        if (g < total) {
+            const int v = __ldg(a.col + bo + (g - eo));
+            const int x = (int)(est_load(a.est + v) & kEstMask);
+            const int y = x < ko ? x : ko;
+#pragma unroll
+            for (int i = 0; i < TW; i++) {
+                const uint32_t m = byte_ramp(y - 4 * i);
+                if (m) atomicAdd(&hist[i * 32 + o], m);
+            }
+        }
+    }
+    __syncwarp();
     int h = 0;
 #pragma unroll
     for (int i = 0; i < TW; i++) {
         const uint32_t thr = (uint32_t)(4 * i + 1) | ((uint32_t)(4 * i + 2) << 8) |
                              ((uint32_t)(4 * i + 3) << 16) | ((uint32_t)(4 * i + 4) << 24);
-        h += __popc(__vcmpgeu4(c[i], thr) & 0x01010101u);
+        h += __popc(__vcmpgeu4(hist[i * 32 + lane], thr) & 0x01010101u);
     }
+    __syncwarp();
     const bool changed = work && h < k;
-    if (changed) acc[kAccUpdates] += 1;
+    if (changed) acc.updates += 1;
     warp_update(S, changed, u, w, h);
-    if (a.refined) return;  // refined activation runs after the update phase
-    const int pmax = __reduce_max_sync(kFull, changed ? d : 0);
-    for (int j = 0; j < pmax; j++) {
+    if (a.sync_mode && a.refined) return;  // activation runs after the update phase
+    if (!__any_sync(kFull, changed)) return;
+    // pass 2: activation.  Cached steps are claimed together.
+    {
+        int pv[kLowCache];
+        uint32_t word[kLowCache];
+        uint32_t cand = 0;
+#pragma unroll
+        for (int c = 0; c < kLowCache; c++) {
+            const int o = co[c];
+            const int ho = __shfl_sync(kFull, h, o), ko = __shfl_sync(kFull, k, o);
+            const bool ch = __shfl_sync(kFull, changed, o);
+            const int x = (int)(cx[c] & kEstMask);
+            pv[c] = cv[c];
+            if (cv[c] >= 0 && ch && x > ho) {
+                cand |= 1u << c;
+                word[c] = (a.refined && x > ko) ? __ldcg(S.bmc + (cv[c] >> 5)) : 0xffffffffu;
+            } else {
+                word[c] = 0xffffffffu;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kLowCache; c++)
+            if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) cand &= ~(1u << c);
+#pragma unroll
+        for (int c = 0; c < kLowCache; c++)
+            word[c] = ((cand >> c) & 1u) ? __ldcg(S.bmn + (pv[c] >> 5)) : 0xffffffffu;
+#pragma unroll
+        for (int c = 0; c < kLowCache; c++) {
+            const uint32_t bit = 1u << (pv[c] & 31);
+            word[c] = (((cand >> c) & 1u) && !(word[c] & bit)) ? atomicOr(S.bmn + (pv[c] >> 5), bit)
+                                                              : 0xffffffffu;
+        }
+#pragma unroll
+        for (int c = 0; c < kLowCache; c++) {
+            const bool fresh = ((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u);
+            if (__any_sync(kFull, fresh)) warp_enqueue(S, Q, fresh, pv[c], cx[c] >> kEstBits, acc);
+        }
+    }
+    for (int g0 = 32 * kLowCache; g0 < total; g0 += 32) {
+        const int g = g0 + lane;
+        const int o = owner_of(g, excl);
+        const long long bo = __shfl_sync(kFull, b, o);
+        const int eo = __shfl_sync(kFull, excl, o);
+        const int ho = __shfl_sync(kFull, h, o), ko = __shfl_sync(kFull, k, o);
+        const bool ch = __shfl_sync(kFull, changed, o);
         bool want = false;
         int v = 0;
-        uint32_t tier = 0;
-        if (changed && j < d) {
-            v = __ldg(a.col + b + j);
-            const uint32_t xw = est_load(a.est + v);
-            want = (uint32_t)h < (xw & kEstMask);
-            tier = xw >> kEstBits;
+        uint32_t xw = 0;
+        if (g < total && ch) {
+            v = __ldg(a.col + bo + (g - eo));
+            xw = est_load(a.est + v);
+            const int x = (int)(xw & kEstMask);
+            want = x > ho && (!a.refined || x <= ko || in_current(S, v));
         }
-        warp_push(S, want, v, tier, acc[kAccPushes]);
+        warp_push(S, Q, want, v, xw >> kEstBits, acc);
     }
 }
 
 // ---------------------------------------------------------------- warp tier
-// One warp per vertex, up to 32*R neighbours held in registers; the count of
-// neighbours >= t comes from a warp reduction, and h by bisection on t after
-// the no-change test t = k.
+// One warp per vertex, up to 32*R neighbour estimates held in registers; the
+// count of neighbours >= t comes from a warp reduction, and h by bisection on
+// t after the no-change test t = k.
 template <typename Off, int R>
-__device__ __forceinline__ void med_vertex(const Sweep& S, const Off* __restrict__ rp, int u,
-                                           unsigned long long acc[kAccN]) {
+__device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
+                                           int u, Acc& acc) {
     const SweepArgs& a = *S.a;
     const int lane = threadIdx.x & 31;
     const long long b = (long long)rp[u];
@@ -200,23 +437,16 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, const Off* __restrict
     const uint32_t w = est_load(a.est + u);
     const int k = (int)(w & kEstMask);
     if (lane == 0) {
-        clear_member(S, u);
-        acc[kAccEvaluated] += 1;
-        acc[kAccDegsum] += (unsigned)d;
+        acc.evaluated += 1;
+        acc.degsum += (unsigned)d;
     }
     if (k == 0) return;
-    uint32_t xw[R];
     int vs[R];
+    uint32_t xw[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int j = r * 32 + lane;
-        vs[r] = 0;
-        xw[r] = 0;
-        if (j < d) {
-            vs[r] = __ldg(a.col + b + j);
-            xw[r] = est_load(a.est + vs[r]);
-        }
-    }
+    for (int r = 0; r < R; r++) vs[r] = (r * 32 + lane < d) ? __ldg(a.col + b + r * 32 + lane) : -1;
+#pragma unroll
+    for (int r = 0; r < R; r++) xw[r] = vs[r] >= 0 ? est_load(a.est + vs[r]) : 0u;
     auto count_ge = [&](int t) {
         int c = 0;
 #pragma unroll
@@ -234,15 +464,14 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, const Off* __restrict
         h = lo;
     }
     if (h >= k) return;
-    if (lane == 0) acc[kAccUpdates] += 1;
+    if (lane == 0) acc.updates += 1;
     warp_update(S, lane == 0, u, w, h);
-    if (a.refined) return;
+    if (a.sync_mode && a.refined) return;
+    uint32_t cand = 0;
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        if (r * 32 >= d) break;
-        const bool want = (r * 32 + lane < d) && (uint32_t)h < (xw[r] & kEstMask);
-        warp_push(S, want, vs[r], xw[r] >> kEstBits, acc[kAccPushes]);
-    }
+    for (int r = 0; r < R; r++)
+        if (vs[r] >= 0 && (int)(xw[r] & kEstMask) > h) cand |= 1u << r;
+    warp_push_n<R>(S, Q, cand, h, k, vs, xw, acc);
 }
 
 // ---------------------------------------------------------------- CTA tier
@@ -273,15 +502,15 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total,
     return r;
 }
 
-// Over buckets i in [0, nb) of s_hist, with above = number of values beyond
-// the last bucket: counts how many i satisfy
-// above + #{values in buckets >= i} >= base + i * width.  The predicate is
-// monotone (true for a prefix of i), so the result minus one is the last i
-// where it holds.  If want_after >= 0, *after gets #{values in buckets >=
-// want_after} + above.
-__device__ __forceinline__ int hub_count_true(const uint32_t* s_hist, int nb, uint32_t above, long long base,
-                              long long width, int want_after, uint32_t* after, uint32_t* wsum,
-                              int* s_int) {
+// Over buckets i in [0, nb) of s_hist, with `above` values beyond the last
+// bucket: counts how many i satisfy
+//   above + #{values in buckets >= i} >= base + i * width.
+// The predicate is monotone (true for a prefix of i), so the count minus one
+// is the last i where it holds.  If want_after >= 0, *after gets
+// above + #{values in buckets >= want_after}.
+__device__ __forceinline__ int hub_count_true(const uint32_t* s_hist, int nb, uint32_t above,
+                                              long long base, long long width, int want_after,
+                                              uint32_t* after, uint32_t* wsum, int* s_int) {
     const int T = blockDim.x, tid = threadIdx.x;
     const int per = (nb + T - 1) / T;
     const int i0 = min(nb, tid * per), i1 = min(nb, i0 + per);
@@ -308,9 +537,9 @@ __device__ __forceinline__ int hub_count_true(const uint32_t* s_hist, int nb, ui
 }
 
 template <typename Off>
-__device__ __forceinline__ void hub_vertex(const Sweep& S, const Off* __restrict__ rp, int u, uint32_t* s_hist,
-                           uint32_t* wsum, int* s_int, uint32_t* s_u32,
-                           unsigned long long acc[kAccN]) {
+__device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
+                                           int u, uint32_t* s_hist, uint32_t* wsum, int* s_int,
+                                           uint32_t* s_u32, Acc& acc) {
     const SweepArgs& a = *S.a;
     const int T = blockDim.x, tid = threadIdx.x;
     const long long b = (long long)rp[u];
@@ -318,9 +547,8 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, const Off* __restrict
     const uint32_t w = est_load(a.est + u);
     const int k = (int)(w & kEstMask);
     if (tid == 0) {
-        clear_member(S, u);
-        acc[kAccEvaluated] += 1;
-        acc[kAccDegsum] += (unsigned long long)d;
+        acc.evaluated += 1;
+        acc.degsum += (unsigned long long)d;
     }
     if (k == 0) return;
     // pass 1: histogram of min(x, k) >> shift, with 2^shift the smallest power
@@ -344,7 +572,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, const Off* __restrict
     if (width == 1) {
         h = istar;
     } else {
-        // above = #{x >= (istar+1) * width}
+        // pass 2: exact counts inside bucket istar; above = #{x >= (istar+1) * width}
         if (tid == 0) *s_u32 = 0;
         __syncthreads();
         hub_count_true(s_hist, nb, 0u, 0, width, istar + 1, s_u32, wsum, s_int);
@@ -367,9 +595,9 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, const Off* __restrict
     }
     __syncthreads();
     if (h >= k) return;
-    if (tid == 0) acc[kAccUpdates] += 1;
+    if (tid == 0) acc.updates += 1;
     if ((tid >> 5) == 0) warp_update(S, tid == 0, u, w, h);
-    if (a.refined) return;
+    if (a.sync_mode && a.refined) return;
     for (long long j0 = 0; j0 < d; j0 += T) {
         const long long j = j0 + tid;
         bool want = false;
@@ -378,37 +606,34 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, const Off* __restrict
         if (j < d) {
             v = __ldg(a.col + b + j);
             const uint32_t xw = est_load(a.est + v);
-            want = (uint32_t)h < (xw & kEstMask);
+            want = should_push(S, h, k, (int)(xw & kEstMask), v);
             tier = xw >> kEstBits;
         }
-        warp_push(S, want, v, tier, acc[kAccPushes]);
+        if (__any_sync(kFull, want)) warp_push(S, Q, want, v, tier, acc);
     }
 }
 
 // ---------------------------------------------------------------- barriers
-// Grid barrier (all CTAs are co-resident: cooperative launch).  Returns false
+// Grid barrier (all CTAs are co-resident: cooperative launch).  bar_count
+// only grows during a launch (it is zeroed before each launch): the k-th
+// barrier of the launch completes when it reaches k * gridDim.  Returns false
 // if the wait ran past the budget; the status word then says TIMEOUT.
-__device__ bool grid_barrier(SweepCtl* ctl, long long timeout_ns, int* s_ok) {
+__device__ bool grid_barrier(SweepCtl* ctl, unsigned& nbar, long long timeout_ns, int* s_ok) {
     __syncthreads();
+    nbar += 1;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = vload(&ctl->bar_gen);
+        const unsigned target = nbar * gridDim.x;
         __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = gtime_ns();
-            while (vload(&ctl->bar_gen) == gen) {
-                if ((long long)(gtime_ns() - t0) > timeout_ns) {
-                    atomicCAS(&ctl->status, 0, (int)KCORE_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        atomicAdd(&ctl->bar_count, 1u);
+        const unsigned long long t0 = gtime_ns();
+        while ((int)(vload(&ctl->bar_count) - target) < 0) {
+            if ((long long)(gtime_ns() - t0) > timeout_ns) {
+                atomicCAS(&ctl->status, 0, (int)KCORE_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            __nanosleep(20);
         }
         __threadfence();
         *s_ok = ok;
@@ -417,20 +642,20 @@ __device__ bool grid_barrier(SweepCtl* ctl, long long timeout_ns, int* s_ok) {
     return *s_ok != 0;
 }
 
-__device__ __forceinline__ void block_barrier() {
-    __threadfence();
-    __syncthreads();
-}
+// One CTA runs the sweep: its own barrier orders its global accesses.
+__device__ __forceinline__ void block_barrier() { __syncthreads(); }
 
 // ---------------------------------------------------------------- kernel
-template <typename Off, int TW, int R>
-__global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
+template <typename Off, int T>
+__global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs a) {
     __shared__ uint32_t s_hist[kHubBins];
     __shared__ uint32_t s_wsum[32];
     __shared__ unsigned long long s_acc[kAccN];
-    __shared__ long long s_b[6];
+    __shared__ long long s_b[12];
     __shared__ int s_int[2];
     __shared__ uint32_t s_u32;
+    __shared__ int s_wbuf[kMaxBlock / 32][kWCap];
+    __shared__ uint32_t s_lowh[kMaxBlock / 32][(T / 4) * 32];
 
     const Off* rp = (const Off*)a.row_ptr;
     SweepCtl* ctl = a.ctl;
@@ -440,6 +665,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
     bool tail = !multi;
     bool prev_tail = tail;
     unsigned my_epoch = 0;
+    unsigned nbar = 0;
+    unsigned long long tot[kAccN] = {0, 0, 0, 0};  // block 0, thread 0: run totals
+    long long tail_sweeps = 0;
     long long s = a.first_sweep;
     if (tid == 0) {
         s_int[0] = 0;
@@ -451,37 +679,53 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
 
     for (;;) {
         const int cur = (int)(s % kSlots), nxt = (int)((s + 1) % kSlots);
+        const int prv = (int)((s + kSlots - 1) % kSlots);
         if (tid == 0) {
-            s_b[0] = vload(&ctl->fcnt[cur][0]);
-            s_b[1] = vload(&ctl->fcnt[cur][1]);
-            s_b[2] = vload(&ctl->fcnt[cur][2]);
-            s_b[3] = vload(&ctl->status);
-            // bookkeeping of sweep s-1 and clearing of its slot
-            if (blockIdx.x == 0 && s > a.first_sweep) {
-                const int ps = (int)((s - 1) % kSlots);
-                unsigned long long v[kAccN];
+            // all loads first (one round trip), then the bookkeeping
+            const unsigned f0 = __ldcg(&ctl->fcnt[cur][0]), f1 = __ldcg(&ctl->fcnt[cur][1]);
+            const unsigned f2 = __ldcg(&ctl->fcnt[cur][2]);
+            const int st = __ldcg(&ctl->status);
+            unsigned pv[kTiers] = {0u, 0u, 0u};
+            unsigned long long av[kAccN] = {0, 0, 0, 0};
+            if (s > 0)
+                for (int q = 0; q < kTiers; q++) pv[q] = __ldcg(&ctl->fcnt[prv][q]);
+            const bool book = blockIdx.x == 0 && s > a.first_sweep;
+            if (book)
+                for (int i = 0; i < kAccN; i++) av[i] = __ldcg(&ctl->acc[prv][i]);
+            s_b[0] = f0;
+            s_b[1] = f1;
+            s_b[2] = f2;
+            s_b[3] = st;
+            for (int q = 0; q < kTiers; q++) s_b[6 + q] = pv[q];
+            if (book) {  // statistics of sweep s-1
                 for (int i = 0; i < kAccN; i++) {
-                    v[i] = vload(&ctl->acc[ps][i]);
-                    ctl->tot[i] += v[i];
-                    ctl->acc[ps][i] = 0;
+                    tot[i] += av[i];
+                    ctl->acc[prv][i] = 0;
                 }
                 if (s - 1 < a.max_trace) {
-                    a.trace[(s - 1) * 3 + 0] = (long long)v[kAccEvaluated];
-                    a.trace[(s - 1) * 3 + 1] = (long long)v[kAccDegsum];
-                    a.trace[(s - 1) * 3 + 2] = (long long)v[kAccUpdates];
+                    a.trace[(s - 1) * 4 + 0] = (long long)av[kAccEvaluated];
+                    a.trace[(s - 1) * 4 + 1] = (long long)av[kAccDegsum];
+                    a.trace[(s - 1) * 4 + 2] = (long long)av[kAccUpdates];
                 }
-                if (prev_tail) ctl->tail_sweeps += 1;
+                if (prev_tail) tail_sweeps += 1;
+            }
+            // start time of sweep s (globaltimer, ns)
+            if (blockIdx.x == 0 && s < a.max_trace) a.trace[s * 4 + 3] = (long long)gtime_ns();
+            // slot of sweep s-2: free now, push target of sweep s+1
+            if (blockIdx.x == 0) {
+                const int old = (int)((s + 2) % kSlots);
                 for (int q = 0; q < 4; q++) {
-                    ctl->fcnt[ps][q] = 0;
-                    ctl->cursor[ps][q] = 0;
+                    ctl->fcnt[old][q] = 0;
+                    ctl->cursor[old][q] = 0;
                 }
-                ctl->ucnt[ps] = 0;
+                ctl->ucnt[old] = 0;
             }
         }
         __syncthreads();
         const unsigned c0 = (unsigned)s_b[0], c1 = (unsigned)s_b[1], c2 = (unsigned)s_b[2];
         const long long total = (long long)c0 + c1 + c2;
         const int status = (int)s_b[3];
+        const long long p0 = s_b[6], p1 = s_b[7], p2 = s_b[8];
         __syncthreads();
 
         // ---- end of the launch?
@@ -490,6 +734,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
         if (status != 0 || finished || capped || s >= a.stop_sweep) {
             if (tid == 0 && blockIdx.x == 0) {
                 ctl->sweep = s;
+                for (int i = 0; i < kAccN; i++) ctl->tot[i] += tot[i];
+                ctl->tail_sweeps += tail_sweeps;
                 if (finished) ctl->done = 1;
                 if (capped) atomicCAS(&ctl->status, 0, (int)KCORE_ERR_NOT_CONVERGED);
             }
@@ -502,10 +748,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
         }
 
         // ---- single-CTA tail transitions
-        if (multi && !tail && total <= a.tail_max) {
-            // Every CTA has read this sweep's counts before CTA 0 goes on alone
-            // (it clears this slot at the start of the next sweep).
-            if (!grid_barrier(ctl, a.timeout_ns, &s_int[1])) return;
+        if (multi && !tail && total <= a.tail_max && c2 == 0) {
+            // Every CTA has read this sweep's counts before CTA 0 goes on alone.
+            if (!grid_barrier(ctl, nbar, a.timeout_ns, &s_int[1])) return;
             if (blockIdx.x != 0) {
                 if (tid == 0) {
                     const unsigned long long t0 = gtime_ns();
@@ -544,63 +789,98 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
             tail = false;
         }
 
-        // ---- phase A: evaluate F_s
+        const int p_cur = (int)(s % kParities), p_nxt = (int)((s + 1) % kParities);
+        const int p_old = (int)((s + 2) % kParities);
         Sweep S;
         S.a = &a;
         S.cur = cur;
         S.nxt = nxt;
-        S.lcur = (s == 0 && a.init_list) ? a.init_list : a.list[s & 1];
-        S.lnxt = a.list[(s + 1) & 1];
-        S.bmc = a.bitmap[s & 1];
-        S.bmn = a.bitmap[(s + 1) & 1];
-        unsigned long long acc[kAccN] = {0, 0, 0, 0};
+        S.lcur = (s == 0 && a.init_list) ? a.init_list : a.list[p_cur];
+        S.lnxt = a.list[p_nxt];
+        S.bmc = a.bitmap[p_cur];
+        S.bmn = a.bitmap[p_nxt];
+        S.wbuf = s_wbuf[wid];
+        WarpQ Q = {{0u, 0u, 0u}};
+        Acc acc = {0, 0, 0, 0};
+        const unsigned warps_all = (tail ? 1u : gridDim.x) * (unsigned)nwarps;
+        const long long gthreads = tail ? blockDim.x : (long long)gridDim.x * blockDim.x;
+        const long long gt = tail ? tid : (long long)blockIdx.x * blockDim.x + tid;
 
-        // CTA tier (hubs first: the longest items)
-        for (;;) {
-            if (tid == 0) s_b[5] = (long long)atomicAdd(&ctl->cursor[cur][2], 1u);
-            __syncthreads();
-            const long long i = s_b[5];
-            __syncthreads();
-            if (i >= c2) break;
-            const int u = list_load(S.lcur + a.tier_off[2] + i);
-            hub_vertex<Off>(S, rp, u, s_hist, s_wsum, &s_int[0], &s_u32, acc);
-            __syncthreads();
-        }
-        // warp tier
-        for (;;) {
-            unsigned base = 0;
-            if (lane == 0) base = atomicAdd(&ctl->cursor[cur][1], (unsigned)a.med_chunk);
-            base = __shfl_sync(kFull, base, 0);
-            if (base >= c1) break;
-            const unsigned end = min(c1, base + (unsigned)a.med_chunk);
-            for (unsigned i = base; i < end; i++) {
-                const int u = list_load(S.lcur + a.tier_off[1] + i);
-                med_vertex<Off, R>(S, rp, u, acc);
+        // ---- clear the membership bits of F_{s-1}: every set bit of bitmap
+        // p_old belongs to it, so zeroing the word of each member is enough
+        if (s > 0) {
+            uint32_t* bmo = a.bitmap[p_old];
+            const long long prev_total = p0 + p1 + p2;
+            if (prev_total >= a.words) {
+                for (long long i = gt; i < a.words; i += gthreads) bmo[i] = 0u;
+            } else {
+                const int* lold = a.list[p_old];
+                for (long long i = gt; i < prev_total; i += gthreads) {
+                    const long long at = i < p0 ? a.tier_off[0] + i
+                                       : i < p0 + p1 ? a.tier_off[1] + (i - p0)
+                                                     : a.tier_off[2] + (i - p0 - p1);
+                    bmo[list_load(lold + at) >> 5] = 0u;
+                }
             }
         }
-        // thread tier
-        for (;;) {
-            unsigned base = 0;
-            const unsigned step = 32u * (unsigned)a.low_chunk;
-            if (lane == 0) base = atomicAdd(&ctl->cursor[cur][0], step);
-            base = __shfl_sync(kFull, base, 0);
-            if (base >= c0) break;
-            for (int r = 0; r < a.low_chunk; r++) {
-                const unsigned i = base + (unsigned)r * 32u + (unsigned)lane;
-                const bool valid = i < c0;
-                const int u = valid ? list_load(S.lcur + a.tier_off[0] + i) : 0;
-                low_vertex<Off, TW>(S, rp, valid, u, acc);
-                if (base + (unsigned)(r + 1) * 32u >= c0) break;
+
+        // ---- phase A: evaluate F_s.  CTA tier first (the longest items).
+        if (c2 > 0) {
+            for (;;) {
+                if (tid == 0) s_b[5] = (long long)atomicAdd(&ctl->cursor[cur][2], 1u);
+                __syncthreads();
+                const long long i = s_b[5];
+                __syncthreads();
+                if (i >= c2) break;
+                const int u = list_load(S.lcur + a.tier_off[2] + i);
+                hub_vertex<Off>(S, Q, rp, u, s_hist, s_wsum, &s_int[0], &s_u32, acc);
+                __syncthreads();
+            }
+        }
+        // warp tier: one warp per vertex, med_chunk vertices per grab (fewer
+        // when the tier is small, so that every warp gets some)
+        if (c1 > 0) {
+            const unsigned wi = max(1u, min((unsigned)a.med_chunk, c1 / warps_all));
+            run_tier(&ctl->cursor[cur][1], c1, wi, [&](unsigned i0, unsigned i1) {
+                for (unsigned i = i0; i < i1; i++) {
+                    const int u = list_load(S.lcur + a.tier_off[1] + i);
+                    med_vertex<Off, kMedR>(S, Q, rp, u, acc);
+                }
+            });
+        }
+        // thread tier: one thread per vertex, 32 * low_chunk vertices per grab.
+        // A large tier is walked by vertex id (dense): membership comes from the
+        // bitmap word, and rows, estimates and adjacency are read coalesced.
+        if (c0 > 0) {
+            if ((long long)c0 * 2 >= a.n) {
+                const unsigned nn = (unsigned)a.n;
+                const unsigned wi = 32u * max(1u, min((unsigned)a.low_chunk, nn / (32u * warps_all)));
+                run_tier(&ctl->cursor[cur][3], nn, wi, [&](unsigned i0, unsigned i1) {
+                    for (unsigned base = i0; base < i1; base += 32u) {
+                        const uint32_t mw = __ldcg(S.bmc + (base >> 5));
+                        const unsigned i = base + (unsigned)lane;
+                        const bool valid = i < i1 && ((mw >> lane) & 1u);
+                        low_warp<Off, T / 4, true>(S, Q, rp, valid, (int)i, s_lowh[wid], acc);
+                    }
+                });
+            } else {
+                const unsigned wi = 32u * max(1u, min((unsigned)a.low_chunk, c0 / (32u * warps_all)));
+                run_tier(&ctl->cursor[cur][0], c0, wi, [&](unsigned i0, unsigned i1) {
+                    for (unsigned base = i0; base < i1; base += 32u) {
+                        const unsigned i = base + (unsigned)lane;
+                        const bool valid = i < i1;
+                        const int u = valid ? list_load(S.lcur + a.tier_off[0] + i) : 0;
+                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, s_lowh[wid], acc);
+                    }
+                });
             }
         }
 
         // ---- synchronous mode: write the recorded updates after a barrier
         if (a.sync_mode) {
             if (tail) block_barrier();
-            else if (!grid_barrier(ctl, a.timeout_ns, &s_int[1])) return;
+            else if (!grid_barrier(ctl, nbar, a.timeout_ns, &s_int[1])) return;
             const unsigned nu = vload(&ctl->ucnt[cur]);
-            const long long gthreads = tail ? blockDim.x : (long long)gridDim.x * blockDim.x;
-            const long long gt = tail ? tid : (long long)blockIdx.x * blockDim.x + tid;
             for (long long i = gt; i < nu; i += gthreads) {
                 const int u = a.upd_list[i];
                 const uint32_t old = est_load(a.est + u);
@@ -609,7 +889,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
             }
             if (a.refined) {
                 if (tail) block_barrier();
-                else if (!grid_barrier(ctl, a.timeout_ns, &s_int[1])) return;
+                else if (!grid_barrier(ctl, nbar, a.timeout_ns, &s_int[1])) return;
                 const long long gw = tail ? nwarps : (long long)gridDim.x * nwarps;
                 const long long wi = tail ? wid : (long long)blockIdx.x * nwarps + wid;
                 for (long long i = wi; i < nu; i += gw) {
@@ -630,19 +910,23 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
                             want = new_u < x && x <= old_u;
                             tier = xw >> kEstBits;
                         }
-                        warp_push(S, want, v, tier, acc[kAccPushes]);
+                        if (__any_sync(kFull, want)) warp_push(S, Q, want, v, tier, acc);
                     }
                 }
             }
         }
+        warp_flush_all(S, Q);
 
         // ---- per-sweep statistics
+        {
+            unsigned long long v4[kAccN] = {acc.evaluated, acc.degsum, acc.updates, acc.pushes};
 #pragma unroll
-        for (int i = 0; i < kAccN; i++) {
-            unsigned long long x = acc[i];
+            for (int i = 0; i < kAccN; i++) {
+                unsigned long long x = v4[i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
-            if (lane == 0 && x) atomicAdd(&s_acc[i], x);
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+                if (lane == 0 && x) atomicAdd(&s_acc[i], x);
+            }
         }
         __syncthreads();
         if (tid < kAccN) {
@@ -653,7 +937,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_sweep(const SweepArgs a) {
         // ---- end of sweep
         prev_tail = tail;
         if (tail) block_barrier();
-        else if (!grid_barrier(ctl, a.timeout_ns, &s_int[1])) return;
+        else if (!grid_barrier(ctl, nbar, a.timeout_ns, &s_int[1])) return;
         s++;
     }
 }
@@ -670,20 +954,9 @@ __global__ void k_output(const uint32_t* __restrict__ est, int* __restrict__ out
         out[v] = (int)(__ldcg(est + v) & kEstMask);
 }
 
-template <typename Off, int TW>
-const void* pick_kernel_tw() {
-    return (const void*)k_sweep<Off, TW, 16>;
-}
-
 const void* pick_kernel(int t_lo, int off64) {
-    if (off64) {
-        if (t_lo <= 8) return pick_kernel_tw<long long, 2>();
-        if (t_lo <= 16) return pick_kernel_tw<long long, 4>();
-        return pick_kernel_tw<long long, 8>();
-    }
-    if (t_lo <= 8) return pick_kernel_tw<int, 2>();
-    if (t_lo <= 16) return pick_kernel_tw<int, 4>();
-    return pick_kernel_tw<int, 8>();
+    (void)t_lo;
+    return off64 ? (const void*)k_sweep<long long, 16> : (const void*)k_sweep<int, 16>;
 }
 
 }  // namespace
@@ -718,6 +991,7 @@ cudaError_t launch_sweep(const SweepArgs& a, int block, int grid_req, int ctas_p
     if (grid < 1) grid = 1;
     *grid_used = grid;
     void* args[] = {(void*)&a};
+    count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, st);
 }
 
@@ -726,6 +1000,7 @@ cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cud
     if (e != cudaSuccess) return e;
     k_ctl_init<<<1, 1, 0, st>>>(ctl, (unsigned)tier_cnt[0], (unsigned)tier_cnt[1],
                                 (unsigned)tier_cnt[2]);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -733,6 +1008,7 @@ cudaError_t launch_output(const uint32_t* est, int* out, long long n, cudaStream
     if (n <= 0) return cudaSuccess;
     const int g = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
     k_output<<<g, 256, 0, st>>>(est, out, n);
+    count_launch();
     return cudaGetLastError();
 }
 
