@@ -206,6 +206,37 @@ kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsu
 /* Release a graph (waits for its outstanding work).  NULL is ignored. */
 void kcore_destroy(kcore_graph* g);
 
+/*
+ * kcore_run_noalloc -- coreness of a clean device CSR without allocating any
+ * memory.  (The paper has no counterpart: this serves callers, not the method.)
+ *
+ * For callers that cannot allocate device memory while they call us: a
+ * serving process that reserved the whole device for its own pool up front,
+ * a real-time loop that must not stall on the allocator's implicit
+ * synchronisation, code running inside another allocator's callback.  The
+ * working memory is one fixed array compiled into the library, sized for
+ * KCORE_NOALLOC_MAX_N vertices (about 19 MB), resident on every GPU that loads
+ * the library until the process exits; the estimates live in coreness_out.
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ *   n             0 <= n <= KCORE_NOALLOC_MAX_N; larger n gives ERR_INVALID.
+ *   row_ptr       DEVICE pointer, n+1 offsets, int32 or int64 per
+ *                 row_ptr_bytes (4 or 8), of a clean CSR: symmetric, rows
+ *                 strictly increasing, no self-loops (the KCORE_IN_CLEAN form).
+ *   col_idx       DEVICE pointer, row_ptr[n] int32 vertex ids.
+ *   coreness_out  DEVICE pointer, n int32, caller-owned; it also holds the
+ *                 estimates while the call runs.
+ * The call is synchronous on `cuda_stream` and returns the run's status
+ * (ERR_INVALID for a malformed CSR, as kcore_run otherwise).  The first call
+ * on each device looks the array's device address up (cudaGetSymbolAddress,
+ * with that device current): make that first call before any stream capture.
+ * Every call shares the one array and finds the previous call's contents in
+ * it; each call clears what must start at zero.  Calls that overlap on the GPU
+ * (on two streams, or from two threads) race on the array: serialise them.
+ */
+#define KCORE_NOALLOC_MAX_N (1 << 19)
+kcore_status kcore_run_noalloc(int64_t n, const void* row_ptr, int32_t row_ptr_bytes,
+                               const int32_t* col_idx, int32_t* coreness_out, void* cuda_stream);
+
 /* ---- batching and serving ------------------------------------------------ */
 /*
  * A batch engine packs many graphs into one device arena and runs them

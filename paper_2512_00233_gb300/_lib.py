@@ -32,6 +32,8 @@ KCORE_SYNC_MODE = 1 << 3
 KCORE_REFINED = 1 << 4
 KCORE_ASYNC = 1 << 5
 
+KCORE_NOALLOC_MAX_N = 1 << 19
+
 STATUS_NAMES = {
     KCORE_OK: "OK", KCORE_PENDING: "PENDING", KCORE_ERR_INVALID: "ERR_INVALID",
     KCORE_ERR_OOM: "ERR_OOM", KCORE_ERR_CUDA: "ERR_CUDA",
@@ -86,6 +88,7 @@ SIGNATURES = {
     "kcore_stats": (c_i32, [c_vp, ctypes.POINTER(RunStats)]),
     "kcore_sweep_trace": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "kcore_destroy": (None, [c_vp]),
+    "kcore_run_noalloc": (c_i32, [c_i64, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "kcore_default_serve_options": (None, [ctypes.POINTER(ServeOptions)]),
     "kcore_batch_create": (c_i32, [ctypes.POINTER(ServeOptions), ctypes.POINTER(c_vp)]),
     "kcore_submit": (c_i32, [c_vp, c_i64, c_vp, c_i32, c_vp, c_u32, ctypes.POINTER(c_u64)]),
