@@ -1,19 +1,816 @@
-// Batch engine placeholder (replaced by the continuous-batching engine).
+// Batch engine: continuous batching of many graphs in one device arena.
+//
+// The arena is one graph over NV vertex slots and NE entries (int64 row_ptr,
+// int32 col_idx, estimates, the three frontier lists with a region per tier,
+// the three membership bitmaps, and the slot of every vertex).  Each admitted
+// graph owns a vertex range and an entry range; the persistent sweep kernel
+// of the single-graph path runs over the whole arena, a chunk of sweeps per
+// launch, so every resident graph advances in the same launch.
+//
+// Between chunks the engine thread
+//   1. retires graphs with no vertex left in the frontier: their estimates are
+//      the coreness (the iteration's fixed point), copied out, ranges freed;
+//   2. admits queued graphs that fit: the whole admission batch is cleaned as
+//      one disjoint union (one device CSR-cleaning call), placed into a
+//      contiguous vertex range (one spare vertex at the end, so the last row
+//      has an end offset), its estimates set to the degrees and every vertex
+//      pushed into the current frontier.
+// A graph admitted while others run joins at the next chunk.  The coreness is
+// unique and the iteration reaches it from any schedule, so each result is
+// the same alone or in any mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "kc_common.cuh"
 
-namespace kc { kcore_status fail(kcore_status s, const std::string& msg); }
+namespace kc {
 
-struct kcore_batch { int unused; };
+kcore_status fail(kcore_status s, const std::string& msg);
+kcore_status cuda_status(cudaError_t e, const char* what);
+void set_error(const std::string& msg);
+kcore_status normalize_options(const kcore_options* in, kcore_options* out);
+cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cudaStream_t st);
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// First-fit allocator of [0, cap) ranges with coalescing on free.
+class Ranges {
+  public:
+    void reset(long long cap) {
+        free_.clear();
+        if (cap > 0) free_[0] = cap;
+        cap_ = cap;
+    }
+    long long take(long long len) {
+        if (len <= 0) return 0;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= len) {
+                const long long at = it->first, rest = it->second - len;
+                free_.erase(it);
+                if (rest > 0) free_[at + len] = rest;
+                used_ += len;
+                peak_ = std::max(peak_, used_);
+                return at;
+            }
+        }
+        return -1;
+    }
+    void give(long long at, long long len) {
+        if (len <= 0) return;
+        used_ -= len;
+        auto next = free_.lower_bound(at);
+        if (next != free_.end() && at + len == next->first) {
+            len += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == at) {
+                prev->second += len;
+                return;
+            }
+        }
+        free_[at] = len;
+    }
+    long long largest() const {
+        long long b = 0;
+        for (auto& kv : free_) b = std::max(b, kv.second);
+        return b;
+    }
+    long long used() const { return used_; }
+    long long peak() const { return peak_; }
+
+  private:
+    std::map<long long, long long> free_;
+    long long cap_ = 0, used_ = 0, peak_ = 0;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    int64_t n = 0;
+    std::vector<int32_t> src, dst;  // raw samples (a CSR input is expanded at submit)
+    // state
+    enum { QUEUED, RESIDENT, DONE } state = QUEUED;
+    bool cancelled = false;
+    kcore_status status = KCORE_OK;
+    std::vector<int32_t> result;
+    double t_submit = 0, t_done = 0;
+    // placement
+    int slot = -1;
+    long long v0 = 0, vlen = 0, e0 = 0, elen = 0;
+};
+
+__device__ __forceinline__ int slot_index(const long long* starts, int count, long long v) {
+    int lo = 0, hi = count - 1;  // last start <= v
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Places the cleaned union (vertices [0, nu), its own row_ptr/col) at arena
+// vertex V0 / entry E0, sets estimates and slots, and pushes every vertex into
+// the current frontier (list and bitmap parity pc, counter slot cs).
+template <typename Off>
+__global__ void k_place(const Off* __restrict__ urp, const int* __restrict__ ucol, long long nu,
+                        long long V0, long long E0, const long long* __restrict__ gstart,
+                        const int* __restrict__ gslot, int ng, int t_lo, int t_hi,
+                        long long* __restrict__ rp, int* __restrict__ col, uint32_t* __restrict__ est,
+                        int* __restrict__ slot_of, int* __restrict__ list, long long NV,
+                        uint32_t* __restrict__ bm, SweepCtl* ctl, int cs) {
+    const int lane = threadIdx.x & 31;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 <= nu;
+         i0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = i0 + threadIdx.x;
+        int tier = -1;
+        long long v = V0 + i;
+        if (i <= nu) {
+            rp[v] = E0 + (long long)urp[i];
+            if (i < nu) {
+                const long long b = (long long)urp[i], e = (long long)urp[i + 1];
+                for (long long j = b; j < e; j++) col[E0 + j] = (int)(V0 + ucol[j]);
+                const long long d = e - b;
+                const int g = slot_index(gstart, ng, i);
+                const bool real = i < gstart[g + 1];  // the spare vertex of a block is not
+                tier = d <= t_lo ? 0 : (d <= t_hi ? 1 : 2);
+                est[v] = ((uint32_t)tier << kEstBits) | (uint32_t)d;
+                slot_of[v] = real ? gslot[g] : -1;
+                if (!real) tier = -1;
+            } else {
+                est[v] = 0;
+                slot_of[v] = -1;
+            }
+        }
+        if (tier >= 0) atomicOr(&bm[v >> 5], 1u << (v & 31));
+#pragma unroll
+        for (int q = 0; q < kTiers; q++) {
+            const unsigned m = __ballot_sync(0xffffffffu, tier == q);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(&ctl->fcnt[cs][q], (unsigned)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (tier == q) list[(long long)q * NV + base + __popc(m & ((1u << lane) - 1u))] = (int)v;
+            }
+        }
+    }
+}
+
+// starts[i] <- row_ptr[starts[i]] (in place: one thread per boundary).
+__global__ void k_gather_rp(const long long* __restrict__ urp, const long long* starts, int count,
+                            long long* out) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const long long v = urp[starts[i]];
+        __syncwarp();
+        out[i] = v;
+    }
+}
+
+// Per-slot count of the vertices in the current frontier.
+__global__ void k_slot_count(const int* __restrict__ list, long long NV, const SweepCtl* ctl, int cs,
+                             const int* __restrict__ slot_of, int* __restrict__ cnt) {
+    for (int q = 0; q < kTiers; q++) {
+        const unsigned c = ctl->fcnt[cs][q];
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c;
+             i += (long long)gridDim.x * blockDim.x) {
+            const int s = slot_of[list[(long long)q * NV + i]];
+            if (s >= 0) atomicAdd(&cnt[s], 1);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace kc
+
+using namespace kc;
+
+struct kcore_batch {
+    kcore_serve_options opt{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // arena
+    long long NV = 0, NE = 0;
+    long long* rp = nullptr;
+    int* col = nullptr;
+    uint32_t* est = nullptr;
+    int* slot_of = nullptr;
+    int* list[kParities] = {nullptr, nullptr, nullptr};
+    uint32_t* bitmap[kParities] = {nullptr, nullptr, nullptr};
+    SweepCtl* ctl = nullptr;
+    long long* trace = nullptr;
+    int* slot_cnt = nullptr;
+    std::vector<int> h_slot_cnt;
+    long long sweep = 0;  // next sweep index of the arena
+    Ranges vr, er;
+    // requests
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, Request*> reqs;
+    std::vector<Request*> slots;
+    std::vector<int> free_slots;
+    uint64_t next_ticket = 1;
+    int resident = 0;
+    // engine
+    std::thread worker;
+    bool stop = false;
+    std::mutex step_mu;  // one engine step at a time
+    // statistics
+    long long submitted = 0, completed = 0, cancelled = 0, failed = 0, launches = 0, sweeps = 0;
+    double busy_s = 0;
+    std::vector<double> latencies;
+};
+
+namespace {
+
+void batch_free(kcore_batch* b) {
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    dfree(b->rp, b->stream);
+    dfree(b->col, b->stream);
+    dfree(b->est, b->stream);
+    dfree(b->slot_of, b->stream);
+    for (int p = 0; p < kParities; p++) {
+        dfree(b->list[p], b->stream);
+        dfree(b->bitmap[p], b->stream);
+    }
+    dfree(b->ctl, b->stream);
+    dfree(b->trace, b->stream);
+    dfree(b->slot_cnt, b->stream);
+    if (b->stream) {
+        cudaStreamSynchronize(b->stream);
+        cudaStreamDestroy(b->stream);
+    }
+    for (auto& kv : b->reqs) delete kv.second;
+    delete b;
+}
+
+// Bytes of arena per vertex slot and per entry.
+constexpr long long kBytesPerVertex = 8 + 4 + 4 + kParities * kTiers * 4 + 1;
+constexpr long long kBytesPerEntry = 4;
+
+// Retire converged graphs.  Called with step_mu held, GPU idle on b->stream.
+kcore_status retire(kcore_batch* b) {
+    const int cs = (int)(b->sweep % kSlots);
+    cudaError_t e = cudaMemsetAsync(b->slot_cnt, 0, sizeof(int) * b->opt.max_slots, b->stream);
+    if (e == cudaSuccess) {
+        k_slot_count<<<152 * 4, 256, 0, b->stream>>>(b->list[b->sweep % kParities], b->NV, b->ctl, cs,
+                                                     b->slot_of, b->slot_cnt);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_slot_cnt.data(), b->slot_cnt, sizeof(int) * b->opt.max_slots,
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e, "batch retire");
+    std::vector<Request*> done;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        for (int s = 0; s < b->opt.max_slots; s++) {
+            Request* r = b->slots[s];
+            if (!r || b->h_slot_cnt[s] != 0) continue;
+            done.push_back(r);
+        }
+    }
+    for (Request* r : done) {
+        std::vector<uint32_t> raw(std::max<int64_t>(r->n, 1));
+        if (r->n)
+            e = cudaMemcpy(raw.data(), b->est + r->v0, sizeof(uint32_t) * r->n, cudaMemcpyDeviceToHost);
+        std::lock_guard<std::mutex> lk(b->mu);
+        if (e != cudaSuccess) {
+            r->status = cuda_status(e, "batch result copy");
+        } else if (!r->cancelled) {
+            r->result.resize(r->n);
+            for (int64_t i = 0; i < r->n; i++) r->result[i] = (int32_t)(raw[i] & kEstMask);
+        }
+        b->vr.give(r->v0, r->vlen);
+        b->er.give(r->e0, r->elen);
+        b->slots[r->slot] = nullptr;
+        b->free_slots.push_back(r->slot);
+        b->resident--;
+        r->state = Request::DONE;
+        r->t_done = now_s();
+        if (r->cancelled) {
+            b->cancelled++;
+        } else if (r->status == KCORE_OK) {
+            b->completed++;
+            b->latencies.push_back(r->t_done - r->t_submit);
+        } else {
+            b->failed++;
+        }
+    }
+    if (!done.empty()) b->cv_done.notify_all();
+    return KCORE_OK;
+}
+
+// Admit queued graphs that fit.  Called with step_mu held, GPU idle.
+kcore_status admit(kcore_batch* b) {
+    std::vector<Request*> batch;
+    long long vtot = 0, etot = 0, samples = 0;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        const long long vfree = b->vr.largest(), efree = b->er.largest();
+        while (!b->queue.empty() && !b->free_slots.empty()) {
+            Request* r = b->queue.front();
+            if (r->cancelled) {
+                b->queue.pop_front();
+                r->state = Request::DONE;
+                b->cancelled++;
+                b->cv_done.notify_all();
+                continue;
+            }
+            const long long v = r->n, ee = 2LL * (long long)r->src.size();
+            if (vtot + v + 1 > vfree || etot + ee > efree) break;
+            b->queue.pop_front();
+            r->slot = b->free_slots.back();
+            b->free_slots.pop_back();
+            batch.push_back(r);
+            vtot += v;
+            etot += ee;
+            samples += (long long)r->src.size();
+        }
+    }
+    if (batch.empty()) return KCORE_OK;
+    // the disjoint union of the batch, one spare vertex at the end
+    const long long nu = vtot + 1;
+    std::vector<int32_t> us(samples), ud(samples);
+    std::vector<long long> gstart(batch.size() + 1);
+    std::vector<int> gslot(batch.size());
+    long long vo = 0, so = 0;
+    for (size_t i = 0; i < batch.size(); i++) {
+        Request* r = batch[i];
+        gstart[i] = vo;
+        gslot[i] = r->slot;
+        for (size_t j = 0; j < r->src.size(); j++) {
+            us[so + j] = (int32_t)(r->src[j] + vo);
+            ud[so + j] = (int32_t)(r->dst[j] + vo);
+        }
+        so += (long long)r->src.size();
+        vo += r->n;
+    }
+    gstart[batch.size()] = vo;
+    std::string err;
+    kcore_status s = KCORE_OK;
+    int *dsrc = nullptr, *dst_ = nullptr;
+    long long* dgs = nullptr;
+    int* dsl = nullptr;
+    DevCsr csr;
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaMallocAsync(&dsrc, sizeof(int) * std::max<long long>(samples, 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dst_, sizeof(int) * std::max<long long>(samples, 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dgs, sizeof(long long) * gstart.size(), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dsl, sizeof(int) * gslot.size(), st);
+    if (e == cudaSuccess && samples)
+        e = cudaMemcpyAsync(dsrc, us.data(), sizeof(int) * samples, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && samples)
+        e = cudaMemcpyAsync(dst_, ud.data(), sizeof(int) * samples, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dgs, gstart.data(), sizeof(long long) * gstart.size(),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dsl, gslot.data(), sizeof(int) * gslot.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_status(e, "batch admission copy");
+    if (s == KCORE_OK) {
+        s = clean_from_coo(nu, samples, dsrc, dst_, 8, st, &csr, &err);
+        if (s != KCORE_OK) set_error(err);
+    }
+    long long V0 = -1, E0 = -1;
+    std::vector<long long> bound(gstart.size(), 0);  // union row_ptr at graph starts
+    if (s == KCORE_OK) {
+        std::lock_guard<std::mutex> lk(b->mu);
+        V0 = b->vr.take(nu);
+        E0 = b->er.take(std::max<long long>(csr.nnz, 1));
+        if (V0 < 0 || E0 < 0) s = fail(KCORE_ERR_OOM, "batch arena fragmented");
+    }
+    if (s == KCORE_OK) {
+        const int cs = (int)(b->sweep % kSlots), pc = (int)(b->sweep % kParities);
+        const int g = (int)std::min<long long>((nu + 256) / 256, 152LL * 16);
+        k_place<long long><<<g, 256, 0, st>>>(
+            (const long long*)csr.row_ptr, csr.col, nu - 1, V0, E0, dgs, dsl, (int)batch.size(),
+            b->opt.sweep.t_lo, b->opt.sweep.t_hi, b->rp, b->col, b->est, b->slot_of, b->list[pc],
+            b->NV, b->bitmap[pc], b->ctl, cs);
+        count_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            k_gather_rp<<<1, 256, 0, st>>>((const long long*)csr.row_ptr, dgs, (int)gstart.size(), dgs);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bound.data(), dgs, sizeof(long long) * gstart.size(),
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_status(e, "batch placement");
+    }
+    cudaFreeAsync(dsrc, st);
+    cudaFreeAsync(dst_, st);
+    cudaFreeAsync(dgs, st);
+    cudaFreeAsync(dsl, st);
+    dfree(csr.row_ptr, st);
+    dfree(csr.col, st);
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (s != KCORE_OK) {
+        if (V0 >= 0) b->vr.give(V0, nu);
+        if (E0 >= 0) b->er.give(E0, std::max<long long>(csr.nnz, 1));
+        for (Request* r : batch) {
+            r->status = s;
+            r->state = Request::DONE;
+            r->t_done = now_s();
+            b->free_slots.push_back(r->slot);
+            b->failed++;
+        }
+        b->cv_done.notify_all();
+        return s;
+    }
+    // per-graph ranges inside the block; the spare vertex and the block's
+    // unused entry slack go with the last graph
+    for (size_t i = 0; i < batch.size(); i++) {
+        Request* r = batch[i];
+        r->v0 = V0 + gstart[i];
+        r->vlen = r->n + (i + 1 == batch.size() ? 1 : 0);
+        r->e0 = E0 + bound[i];
+        r->elen = (i + 1 == batch.size() ? std::max<long long>(csr.nnz, 1) : bound[i + 1]) - bound[i];
+        r->state = Request::RESIDENT;
+        b->slots[r->slot] = r;
+        b->resident++;
+    }
+    return KCORE_OK;
+}
+
+// One chunk of sweeps over the whole arena.  GPU idle on entry and exit.
+kcore_status run_chunk(kcore_batch* b) {
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.row_ptr = b->rp;
+    a.col = b->col;
+    a.est = b->est;
+    a.init_list = nullptr;
+    for (int p = 0; p < kParities; p++) {
+        a.list[p] = b->list[p];
+        a.bitmap[p] = b->bitmap[p];
+    }
+    a.tier_off[0] = 0;
+    a.tier_off[1] = b->NV;
+    a.tier_off[2] = 2 * b->NV;
+    a.ctl = b->ctl;
+    a.trace = nullptr;
+    a.max_trace = 0;
+    a.first_sweep = b->sweep;
+    a.max_sweeps = LLONG_MAX;
+    a.stop_sweep = b->sweep + b->opt.chunk_sweeps;
+    a.timeout_ns = (long long)(b->opt.sweep.timeout_s * 1e9);
+    a.words = (b->NV + 31) / 32;
+    a.n = (int)b->NV;
+    a.t_lo = b->opt.sweep.t_lo;
+    a.t_hi = b->opt.sweep.t_hi;
+    a.low_chunk = b->opt.sweep.low_chunk;
+    a.med_chunk = b->opt.sweep.med_chunk;
+    a.tail_max = b->opt.sweep.tail_max < 0 ? 0 : b->opt.sweep.tail_max;
+    a.off64 = 1;
+    // the grid barrier counter restarts at zero for every launch
+    cudaError_t e = cudaMemsetAsync(&b->ctl->bar_count, 0, sizeof(unsigned), b->stream);
+    int grid = 0;
+    if (e == cudaSuccess)
+        e = launch_sweep(a, b->opt.sweep.block, b->opt.sweep.max_ctas, b->opt.sweep.ctas_per_sm,
+                         b->stream, &grid);
+    long long hs[2] = {0, 0};  // sweep, status+done
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hs[0], &b->ctl->sweep, sizeof(long long), cudaMemcpyDeviceToHost, b->stream);
+    int st2[2] = {0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st2, &b->ctl->status, sizeof(int) * 2, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e, "batch sweep launch");
+    b->launches++;
+    b->sweeps += hs[0] - b->sweep;
+    b->sweep = hs[0];
+    if (st2[0] != 0) return fail((kcore_status)st2[0], "batch sweep kernel reported an error");
+    return KCORE_OK;
+}
+
+kcore_status step(kcore_batch* b, int64_t* active) {
+    std::lock_guard<std::mutex> sl(b->step_mu);
+    cudaSetDevice(b->device);
+    const double t0 = now_s();
+    kcore_status s = admit(b);
+    bool any;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        any = b->resident > 0;
+    }
+    if (s == KCORE_OK && any) s = run_chunk(b);
+    if (s == KCORE_OK && any) s = retire(b);
+    if (any) b->busy_s += now_s() - t0;
+    if (active) {
+        std::lock_guard<std::mutex> lk(b->mu);
+        *active = b->resident + (int64_t)b->queue.size();
+    }
+    if (s != KCORE_OK) {
+        // fail everything resident: the arena state is no longer trusted
+        std::lock_guard<std::mutex> lk(b->mu);
+        for (int i = 0; i < b->opt.max_slots; i++) {
+            Request* r = b->slots[i];
+            if (!r) continue;
+            r->status = s;
+            r->state = Request::DONE;
+            r->t_done = now_s();
+            b->slots[i] = nullptr;
+            b->free_slots.push_back(i);
+            b->resident--;
+            b->failed++;
+        }
+        b->vr.reset(b->NV);
+        b->er.reset(b->NE);
+        b->cv_done.notify_all();
+    }
+    return s;
+}
+
+void engine_loop(kcore_batch* b) {
+    cudaSetDevice(b->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(b->mu);
+            b->cv_work.wait(lk, [&] { return b->stop || !b->queue.empty() || b->resident > 0; });
+            if (b->stop) return;
+        }
+        step(b, nullptr);
+    }
+}
+
+kcore_status enqueue(kcore_batch* b, Request* r, uint64_t* ticket) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    if ((long long)b->queue.size() >= b->opt.max_queue) {
+        delete r;
+        return fail(KCORE_ERR_AGAIN, "batch queue is full");
+    }
+    if (r->n + 1 > b->NV || 2LL * (long long)r->src.size() > b->NE) {
+        delete r;
+        return fail(KCORE_ERR_AGAIN, "graph can never fit the batch arena");
+    }
+    r->ticket = b->next_ticket++;
+    r->t_submit = now_s();
+    b->reqs[r->ticket] = r;
+    b->queue.push_back(r);
+    b->submitted++;
+    *ticket = r->ticket;
+    b->cv_work.notify_one();
+    return KCORE_OK;
+}
+
+}  // namespace
 
 extern "C" {
-void kcore_default_serve_options(kcore_serve_options* o) { if (o) { memset(o, 0, sizeof(*o)); o->struct_size = sizeof(*o); } }
-kcore_status kcore_batch_create(const kcore_serve_options*, kcore_batch** out) { if (out) *out = nullptr; return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-kcore_status kcore_submit(kcore_batch*, int64_t, const void*, int32_t, const int32_t*, uint32_t, uint64_t*) { return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-kcore_status kcore_submit_coo(kcore_batch*, int64_t, int64_t, const int32_t*, const int32_t*, uint32_t, uint64_t*) { return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-kcore_status kcore_poll(kcore_batch*, uint64_t, int32_t*, int64_t) { return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-kcore_status kcore_cancel(kcore_batch*, uint64_t) { return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-kcore_status kcore_batch_step(kcore_batch*, int64_t*) { return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-kcore_status kcore_batch_stats_get(kcore_batch*, kcore_batch_stats*) { return kc::fail(KCORE_ERR_INVALID, "batch engine not built"); }
-void kcore_batch_destroy(kcore_batch*) {}
+
+void kcore_default_serve_options(kcore_serve_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(*o);
+    o->mem_budget = 4LL << 30;
+    o->max_slots = 4096;
+    o->max_queue = 1 << 20;
+    o->chunk_sweeps = 16;
+    o->start_thread = 1;
+    kcore_default_options(&o->sweep);
 }
+
+kcore_status kcore_batch_create(const kcore_serve_options* opt, kcore_batch** out) {
+    if (!out) return fail(KCORE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    kcore_serve_options o;
+    kcore_default_serve_options(&o);
+    if (opt) {
+        if (opt->struct_size != 0 && opt->struct_size < sizeof(kcore_serve_options))
+            return fail(KCORE_ERR_INVALID, "kcore_serve_options.struct_size too small");
+        if (opt->mem_budget) o.mem_budget = opt->mem_budget;
+        if (opt->max_slots) o.max_slots = opt->max_slots;
+        if (opt->max_queue) o.max_queue = opt->max_queue;
+        if (opt->chunk_sweeps) o.chunk_sweeps = opt->chunk_sweeps;
+        o.start_thread = opt->start_thread;
+        if (opt->sweep.struct_size) o.sweep = opt->sweep;
+    }
+    kcore_options norm;
+    kcore_status ns = normalize_options(&o.sweep, &norm);
+    if (ns != KCORE_OK) return ns;
+    o.sweep = norm;
+    if (o.mem_budget < (16LL << 20) || o.max_slots < 1 || o.max_queue < 1 || o.chunk_sweeps < 1)
+        return fail(KCORE_ERR_INVALID, "bad serve options");
+    kcore_batch* b = new kcore_batch();
+    b->opt = o;
+    cudaGetDevice(&b->device);
+    // split the budget: a third for entries beyond 8 per vertex keeps typical
+    // sparse graphs balanced
+    const long long per_v = kBytesPerVertex + 8 * kBytesPerEntry;
+    b->NV = std::min<long long>(o.mem_budget / per_v, (long long)INT_MAX - 1);
+    b->NE = (o.mem_budget - b->NV * kBytesPerVertex) / kBytesPerEntry;
+    b->NV = b->NV / 32 * 32;
+    std::string err;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_status(e, "batch stream");
+    }
+    kcore_status s = KCORE_OK;
+    auto al = [&](void** p, size_t bytes) {
+        if (s == KCORE_OK) s = dmalloc(p, bytes, &err, b->stream);
+    };
+    al((void**)&b->rp, sizeof(long long) * (b->NV + 1));
+    al((void**)&b->col, sizeof(int) * std::max<long long>(b->NE, 1));
+    al((void**)&b->est, sizeof(uint32_t) * b->NV);
+    al((void**)&b->slot_of, sizeof(int) * b->NV);
+    for (int p = 0; p < kParities; p++) {
+        al((void**)&b->list[p], sizeof(int) * kTiers * b->NV);
+        al((void**)&b->bitmap[p], sizeof(uint32_t) * (b->NV / 32 + 1));
+    }
+    al((void**)&b->ctl, sizeof(SweepCtl));
+    al((void**)&b->slot_cnt, sizeof(int) * o.max_slots);
+    if (s != KCORE_OK) {
+        set_error(err);
+        batch_free(b);
+        return s;
+    }
+    const long long zero[kTiers] = {0, 0, 0};
+    e = launch_ctl_init(b->ctl, zero, b->stream);
+    for (int p = 0; p < kParities && e == cudaSuccess; p++)
+        e = cudaMemsetAsync(b->bitmap[p], 0, sizeof(uint32_t) * (b->NV / 32 + 1), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->slot_of, 0xff, sizeof(int) * b->NV, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_status(e, "batch init");
+    }
+    b->h_slot_cnt.assign(o.max_slots, 0);
+    b->slots.assign(o.max_slots, nullptr);
+    for (int i = o.max_slots - 1; i >= 0; i--) b->free_slots.push_back(i);
+    b->vr.reset(b->NV);
+    b->er.reset(b->NE);
+    if (o.start_thread) b->worker = std::thread(engine_loop, b);
+    *out = b;
+    return KCORE_OK;
+}
+
+kcore_status kcore_submit_coo(kcore_batch* b, int64_t n, int64_t nnz, const int32_t* src,
+                              const int32_t* dst, uint32_t flags, uint64_t* ticket) {
+    if (!b || !ticket) return fail(KCORE_ERR_INVALID, "NULL argument");
+    if (flags & KCORE_IN_DEVICE) return fail(KCORE_ERR_INVALID, "batch input must be host arrays");
+    if (n < 0 || n >= INT_MAX || nnz < 0 || (nnz > 0 && (!src || !dst)))
+        return fail(KCORE_ERR_INVALID, "bad graph arguments");
+    Request* r = new Request();
+    r->n = n;
+    r->src.assign(src, src + nnz);
+    r->dst.assign(dst, dst + nnz);
+    for (int64_t i = 0; i < nnz; i++)
+        if ((uint32_t)src[i] >= (uint64_t)n || (uint32_t)dst[i] >= (uint64_t)n) {
+            delete r;
+            return fail(KCORE_ERR_INVALID, "edge endpoint outside [0, n)");
+        }
+    return enqueue(b, r, ticket);
+}
+
+kcore_status kcore_submit(kcore_batch* b, int64_t n, const void* row_ptr, int32_t row_ptr_bytes,
+                          const int32_t* col_idx, uint32_t flags, uint64_t* ticket) {
+    if (!b || !ticket || !row_ptr) return fail(KCORE_ERR_INVALID, "NULL argument");
+    if (flags & KCORE_IN_DEVICE) return fail(KCORE_ERR_INVALID, "batch input must be host arrays");
+    if (row_ptr_bytes != 4 && row_ptr_bytes != 8) return fail(KCORE_ERR_INVALID, "row_ptr_bytes");
+    if (n < 0 || n >= INT_MAX) return fail(KCORE_ERR_INVALID, "bad n");
+    auto at = [&](int64_t i) -> int64_t {
+        return row_ptr_bytes == 8 ? ((const int64_t*)row_ptr)[i] : ((const int32_t*)row_ptr)[i];
+    };
+    const int64_t nnz = at(n);
+    if (at(0) != 0 || nnz < 0 || (nnz > 0 && !col_idx))
+        return fail(KCORE_ERR_INVALID, "row_ptr must start at 0 and end at nnz >= 0");
+    Request* r = new Request();
+    r->n = n;
+    r->src.resize(nnz);
+    r->dst.resize(nnz);
+    for (int64_t u = 0; u < n; u++) {
+        const int64_t lo = at(u), hi = at(u + 1);
+        if (hi < lo || hi > nnz) {
+            delete r;
+            return fail(KCORE_ERR_INVALID, "row_ptr must be non-decreasing");
+        }
+        for (int64_t j = lo; j < hi; j++) {
+            if ((uint32_t)col_idx[j] >= (uint64_t)n) {
+                delete r;
+                return fail(KCORE_ERR_INVALID, "col_idx entry outside [0, n)");
+            }
+            r->src[j] = (int32_t)u;
+            r->dst[j] = col_idx[j];
+        }
+    }
+    return enqueue(b, r, ticket);
+}
+
+kcore_status kcore_poll(kcore_batch* b, uint64_t ticket, int32_t* coreness_out, int64_t timeout_us) {
+    if (!b) return fail(KCORE_ERR_INVALID, "NULL batch");
+    std::unique_lock<std::mutex> lk(b->mu);
+    auto it = b->reqs.find(ticket);
+    if (it == b->reqs.end()) return fail(KCORE_ERR_INVALID, "unknown ticket");
+    Request* r = it->second;
+    auto ready = [&] { return r->state == Request::DONE; };
+    if (!ready()) {
+        if (timeout_us == 0) return KCORE_PENDING;
+        if (!b->opt.start_thread) {
+            // no engine thread: drive the engine from here
+            lk.unlock();
+            const double t_end = timeout_us < 0 ? 1e300 : now_s() + timeout_us * 1e-6;
+            for (;;) {
+                int64_t active = 0;
+                kcore_status s = step(b, &active);
+                (void)s;
+                lk.lock();
+                if (ready() || now_s() > t_end) break;
+                lk.unlock();
+            }
+        } else if (timeout_us < 0) {
+            b->cv_done.wait(lk, ready);
+        } else {
+            b->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+        }
+        if (!ready()) return KCORE_PENDING;
+    }
+    kcore_status s = r->cancelled ? KCORE_ERR_CANCELLED : r->status;
+    if (s == KCORE_OK && coreness_out && r->n)
+        memcpy(coreness_out, r->result.data(), sizeof(int32_t) * r->n);
+    b->reqs.erase(it);
+    delete r;
+    if (s < 0) set_error(s == KCORE_ERR_CANCELLED ? "request was cancelled" : "request failed");
+    return s;
+}
+
+kcore_status kcore_cancel(kcore_batch* b, uint64_t ticket) {
+    if (!b) return fail(KCORE_ERR_INVALID, "NULL batch");
+    std::lock_guard<std::mutex> lk(b->mu);
+    auto it = b->reqs.find(ticket);
+    if (it == b->reqs.end()) return fail(KCORE_ERR_INVALID, "unknown ticket");
+    it->second->cancelled = true;
+    b->cv_work.notify_one();
+    return KCORE_OK;
+}
+
+kcore_status kcore_batch_step(kcore_batch* b, int64_t* active) {
+    if (!b) return fail(KCORE_ERR_INVALID, "NULL batch");
+    if (b->opt.start_thread) return fail(KCORE_ERR_INVALID, "the engine runs its own thread");
+    return step(b, active);
+}
+
+kcore_status kcore_batch_stats_get(kcore_batch* b, kcore_batch_stats* out) {
+    if (!b || !out) return fail(KCORE_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(b->mu);
+    memset(out, 0, sizeof(*out));
+    out->submitted = b->submitted;
+    out->completed = b->completed;
+    out->cancelled = b->cancelled;
+    out->failed = b->failed;
+    out->queued = (int64_t)b->queue.size();
+    out->resident = b->resident;
+    out->launches = b->launches;
+    out->sweeps = b->sweeps;
+    out->arena_bytes = b->NV * kBytesPerVertex + b->NE * kBytesPerEntry;
+    out->arena_used_peak = b->vr.peak() * kBytesPerVertex + b->er.peak() * kBytesPerEntry;
+    out->busy_s = b->busy_s;
+    if (!b->latencies.empty()) {
+        std::vector<double> l = b->latencies;
+        std::sort(l.begin(), l.end());
+        auto q = [&](double p) {
+            const size_t i = (size_t)std::min<double>(l.size() - 1, std::max(0.0, p * (l.size() - 1)));
+            return l[i] * 1e3;
+        };
+        out->latency_p50_ms = q(0.50);
+        out->latency_p99_ms = q(0.99);
+    }
+    return KCORE_OK;
+}
+
+void kcore_batch_destroy(kcore_batch* b) {
+    if (!b) return;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->stop = true;
+        b->cv_work.notify_all();
+    }
+    if (b->worker.joinable()) b->worker.join();
+    batch_free(b);
+}
+
+}  // extern "C"
