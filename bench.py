@@ -63,37 +63,75 @@ def dist_env():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi SM clock / throttle reasons sampled every 100 ms."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """SM clock, max clock and throttle reasons sampled every millisecond
+    during the timed region through NVML (read-only queries via ctypes), or
+    every 100 ms through nvidia-smi when NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = str(index)
+        self.bus = None
         try:
             import torch
-            bus = getattr(torch.cuda.get_device_properties(index), "pci_bus_id", None)
-            if bus is not None:
-                dom = getattr(torch.cuda.get_device_properties(index), "pci_domain_id", 0)
-                dv = getattr(torch.cuda.get_device_properties(index), "pci_device_id", 0)
-                self.index = f"{dom:08X}:{bus:02X}:{dv:02X}.0"
+            p = torch.cuda.get_device_properties(index)
+            self.bus = f"{getattr(p, 'pci_domain_id', 0):08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
         except Exception:
             pass
-        self.samples = []
+        self.index = index
+        self.samples = []      # (sm_mhz, max_mhz, reason bits)
         self._stop = threading.Event()
         self._t = None
+        self._nvml = self._open_nvml()
+
+    def _open_nvml(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            ok = -1
+            if self.bus:
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(self.bus.encode(), ctypes.byref(h))
+            if ok != 0:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(h))
+            if ok != 0:
+                return None
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            return lib, h, reasons
+        except Exception:
+            return None
+
+    def _sample_nvml(self):
+        import ctypes
+        lib, h, reasons = self._nvml
+        c, m, r = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(c))
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(m))
+        reasons(h, ctypes.byref(r))
+        self.samples.append((float(c.value), float(m.value), int(r.value)))
+
+    def _sample_smi(self):
+        out = subprocess.run(["nvidia-smi", f"--id={self.bus or self.index}", f"--query-gpu={self.Q}",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=5).stdout.strip()
+        f = [x.strip() for x in out.split(",")]
+        if len(f) >= 6 and f[0].replace(".", "").isdigit():
+            bits = sum(b for b, v in zip((0x8, 0x40, 0x20, 0x4), f[2:6]) if v.lower() == "active")
+            self.samples.append((float(f[0]), float(f[1]), bits))
 
     def _run(self):
+        period = 0.001 if self._nvml else 0.1
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
+                self._sample_nvml() if self._nvml else self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.1)
+            self._stop.wait(period)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -103,16 +141,22 @@ class ClockSampler:
     def __exit__(self, *exc):
         self._stop.set()
         self._t.join(timeout=10)
+        if not self.samples:          # a region shorter than one sample: take one now
+            try:
+                self._sample_nvml() if self._nvml else self._sample_smi()
+            except Exception:
+                pass
 
     def summary(self):
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        sm = [x[0] for x in self.samples]
+        mx = [x[1] for x in self.samples]
+        bits = 0
+        for x in self.samples:
+            bits |= x[2]
+        reasons = sorted(name for b, name in self.REASONS.items() if bits & b)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi"}
 
 
 def measured_peaks():

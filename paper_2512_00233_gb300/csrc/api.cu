@@ -80,6 +80,8 @@ struct kcore_graph {
     long long max_trace = 0;
     long long tier_cnt[kTiers] = {0, 0, 0};
     SweepCtl* hctl = nullptr;  // pinned copy of the control block after a run
+    TierOut* htier = nullptr;  // pinned copy of the tier split results (same block)
+    TierOut* dtier = nullptr;  // device tier split results
     cudaEvent_t ev[6] = {};    // create0, create1, run0, sweep0, sweep1, run1
     bool pending = false;
     bool ran = false;
@@ -111,11 +113,30 @@ void release(kcore_graph* g) {
     dfree(g->upd_val);
     dfree(g->ctl);
     dfree(g->trace);
+    dfree(g->dtier);
     if (g->hctl) pinned_put(g->hctl);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     cudaSetDevice(prev);
     delete g;
+}
+
+// The one wait of graph creation: tier sizes, row_ptr[n] and the degree check.
+kcore_status read_tiers(kcore_graph* g, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(g->htier, g->dtier, sizeof(TierOut), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "tier split");
+    const TierOut& t = *g->htier;
+    if (t.bad) return fail(KCORE_ERR_INVALID, "a vertex degree is 2^30 or more");
+    for (int q = 0; q < kTiers; q++) g->tier_cnt[q] = (long long)t.bound[q + 1] - t.bound[q];
+    if (g->csr.n == 0) {
+        g->csr.nnz = 0;
+    } else {
+        g->csr.nnz = t.nnz;
+        if (g->csr.off_bytes == 4 && g->csr.nnz > 0x7fffffffLL)
+            return fail(KCORE_ERR_INVALID, "cleaned graph has 2m >= 2^31 entries; use 8-byte row_ptr");
+    }
+    return KCORE_OK;
 }
 
 // Allocates the per-run state and splits the vertices into degree tiers.
@@ -139,15 +160,18 @@ kcore_status finish_graph(kcore_graph* g, cudaStream_t st) {
     KC_ALLOC(g->ctl, sizeof(SweepCtl));
     g->max_trace = 1 << 16;
     KC_ALLOC(g->trace, sizeof(long long) * 4 * g->max_trace);
+    KC_ALLOC(g->dtier, sizeof(TierOut));
 #undef KC_ALLOC
-    static_assert(sizeof(SweepCtl) <= kPinnedBlock, "control block copy does not fit");
-    cudaError_t e = pinned_get((void**)&g->hctl, sizeof(SweepCtl));
+    static_assert(sizeof(SweepCtl) <= 2048 && sizeof(TierOut) <= kPinnedBlock - 2048,
+                  "pinned block layout");
+    cudaError_t e = pinned_get((void**)&g->hctl, kPinnedBlock);
     if (e != cudaSuccess) return cuda_status(e, "pinned host block");
     memset(g->hctl, 0, sizeof(SweepCtl));
+    g->htier = (TierOut*)((char*)g->hctl + 2048);
     s = tier_split(n, g->csr.row_ptr, g->csr.off_bytes, g->opt.t_lo, g->opt.t_hi, g->est0,
-                   g->init_list, g->tier_cnt, st, &err);
+                   g->init_list, g->dtier, st, &err);
     if (s != KCORE_OK) return fail(s, err);
-    return KCORE_OK;
+    return read_tiers(g, st);
 }
 
 kcore_status begin_create(int64_t n, int32_t row_ptr_bytes, const kcore_options* opt,
@@ -177,7 +201,7 @@ kcore_status begin_create(int64_t n, int32_t row_ptr_bytes, const kcore_options*
 // Host input -> temporary device copy.
 template <typename T>
 kcore_status upload(const T* host, size_t count, cudaStream_t st, T** dev) {
-    cudaError_t e = cudaMallocAsync((void**)dev, std::max<size_t>(count, 1) * sizeof(T), st);
+    cudaError_t e = pool_alloc((void**)dev, std::max<size_t>(count, 1) * sizeof(T), st);
     if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (input copy)");
     if (count) {
         e = cudaMemcpyAsync(*dev, host, count * sizeof(T), cudaMemcpyHostToDevice, st);
@@ -376,9 +400,9 @@ kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* c
     std::string err;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s = tier_split(g->csr.n, g->csr.row_ptr, g->csr.off_bytes, o.t_lo, o.t_hi, g->est0,
-                   g->init_list, g->tier_cnt, st, &err);
+                   g->init_list, g->dtier, st, &err);
     if (s != KCORE_OK) return fail(s, err);
-    return KCORE_OK;
+    return read_tiers(g, st);
 }
 
 kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, void* cuda_stream) {

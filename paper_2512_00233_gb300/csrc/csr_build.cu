@@ -123,9 +123,9 @@ cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStre
         return cudaGetLastError();
     }
     unsigned long long *bsum = nullptr, *boff = nullptr;
-    cudaError_t e = cudaMallocAsync(&bsum, sizeof(unsigned long long) * nb, st);
+    cudaError_t e = pool_alloc((void**)&bsum, sizeof(unsigned long long) * nb, st);
     if (e != cudaSuccess) return e;
-    e = cudaMallocAsync(&boff, sizeof(unsigned long long) * (nb + 1), st);
+    e = pool_alloc((void**)&boff, sizeof(unsigned long long) * (nb + 1), st);
     if (e != cudaSuccess) {
         cudaFreeAsync(bsum, st);
         return e;
@@ -530,9 +530,9 @@ cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long l
     if (N <= 1) return cudaSuccess;
     const long long nt = (N + kRsTile - 1) / kRsTile;
     uint32_t *hist = nullptr, *off = nullptr;
-    cudaError_t e = cudaMallocAsync(&hist, sizeof(uint32_t) * 256 * nt, st);
+    cudaError_t e = pool_alloc((void**)&hist, sizeof(uint32_t) * 256 * nt, st);
     if (e != cudaSuccess) return e;
-    e = cudaMallocAsync(&off, sizeof(uint32_t) * 256 * nt, st);
+    e = pool_alloc((void**)&off, sizeof(uint32_t) * 256 * nt, st);
     if (e != cudaSuccess) {
         cudaFreeAsync(hist, st);
         return e;
@@ -710,6 +710,14 @@ __global__ void __launch_bounds__(kTsT) k_tier_write(const Off* __restrict__ rp,
     }
 }
 
+// Gathers the tier boundaries and row_ptr[n] into the block the host reads.
+__global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int off_bytes,
+                           long long n, TierOut* out) {
+    if (threadIdx.x <= kTiers) out->bound[threadIdx.x] = off[(long long)threadIdx.x * nb];
+    if (threadIdx.x == 0)
+        out->nnz = off_bytes == 8 ? ((const long long*)row_ptr)[n] : (long long)((const int*)row_ptr)[n];
+}
+
 int id_bits(long long n) {
     int b = 0;
     while ((1ll << b) < n) b++;
@@ -725,7 +733,7 @@ struct Temp {
     }
     template <typename T>
     cudaError_t get(T** p, size_t count) {
-        cudaError_t e = cudaMallocAsync((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
+        cudaError_t e = pool_alloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
@@ -765,17 +773,15 @@ cudaError_t compact(int64_t n, const uint32_t* off, const uint32_t* seg, const u
 
 // Steps 2-5, after the counts are in cnt.  `scatter` launches step 3.
 template <typename ScatterFn>
-kcore_status finish(Temp& tmp, int64_t n, uint32_t* cnt, BuildCtl* bc, int off_bytes,
+kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* bc, int off_bytes,
                     cudaStream_t st, DevCsr* out, std::string* err, ScatterFn scatter) {
+    // N: an upper bound of the entries (two per input sample or entry)
     const long long nn = std::max<int64_t>(n, 1);
     uint32_t *off = nullptr, *seg = nullptr, *ucnt = nullptr;
     int *mid = nullptr, *big = nullptr, *huge = nullptr;
     KC_TRY(tmp.get(&off, (size_t)nn + 1), "row offsets");
     KC_TRY(exclusive_scan(ReadU32{cnt}, n, off, true, st), "offset scan");
-    uint32_t N = 0;
     BuildCtl hbc;
-    KC_TRY(cudaMemcpyAsync(&N, off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "read size");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
     KC_TRY(tmp.get(&seg, (size_t)N), "segments");
     KC_TRY(tmp.get(&ucnt, (size_t)nn), "distinct counts");
     KC_TRY(tmp.get(&mid, (size_t)nn), "row lists");
@@ -844,13 +850,8 @@ kcore_status finish(Temp& tmp, int64_t n, uint32_t* cnt, BuildCtl* bc, int off_b
             KC_TRY(compact(n, off, seg, ucnt, (const int*)out->row_ptr, out->col, lists, counts, hc,
                            st), "compact");
     }
-    long long nnz = 0;
-    KC_TRY(cudaMemcpyAsync(&nnz, (const char*)out->row_ptr + (size_t)off_bytes * n, off_bytes,
-                           cudaMemcpyDeviceToHost, st), "read nnz");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
-    if (off_bytes == 4) nnz = (long long)(int32_t)(nnz & 0xffffffffLL);
     out->n = n;
-    out->nnz = nnz;
+    out->nnz = -1;  // row_ptr[n], read by the caller's next wait
     out->off_bytes = off_bytes;
     return KCORE_OK;
 }
@@ -880,7 +881,7 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
         count_launch();
         KC_TRY(cudaGetLastError(), "count");
     }
-    kcore_status s = finish(tmp, n, cnt, bc, off_bytes, st, out, err,
+    kcore_status s = finish(tmp, n, 2 * (long long)samples, cnt, bc, off_bytes, st, out, err,
                             [&](const uint32_t* off, uint32_t* fill, uint32_t* seg) {
                                 if (samples == 0) return cudaSuccess;
                                 k_scatter_coo<<<grid_for(samples, 256), 256, 0, st>>>(
@@ -888,10 +889,6 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
                                 count_launch();
                                 return cudaGetLastError();
                             });
-    if (s == KCORE_OK && off_bytes == 4 && out->nnz > 0x7fffffffLL) {
-        *err = "cleaned graph has 2m >= 2^31 entries; use 8-byte row_ptr";
-        return KCORE_ERR_INVALID;
-    }
     return s;
 }
 
@@ -918,7 +915,7 @@ kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, co
         count_launch();
         KC_TRY(cudaGetLastError(), "count");
     }
-    kcore_status s = finish(tmp, n, cnt, bc, off_bytes, st, out, err,
+    kcore_status s = finish(tmp, n, 2 * (long long)nnz, cnt, bc, off_bytes, st, out, err,
                             [&](const uint32_t* off, uint32_t* fill, uint32_t* seg) {
                                 if (n == 0) return cudaSuccess;
                                 if (in_off_bytes == 8)
@@ -930,10 +927,6 @@ kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, co
                                 count_launch();
                                 return cudaGetLastError();
                             });
-    if (s == KCORE_OK && off_bytes == 4 && out->nnz > 0x7fffffffLL) {
-        *err = "cleaned graph has 2m >= 2^31 entries; use 8-byte row_ptr";
-        return KCORE_ERR_INVALID;
-    }
     return s;
 }
 
@@ -963,22 +956,20 @@ kcore_status check_clean_csr(int64_t n, const void* row_ptr, int off_bytes, cons
 }
 
 kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo, int t_hi,
-                        uint32_t* est0, int* init_list, long long tier_cnt[kTiers],
-                        cudaStream_t st, std::string* err) {
-    for (int q = 0; q < kTiers; q++) tier_cnt[q] = 0;
+                        uint32_t* est0, int* init_list, TierOut* dout, cudaStream_t st,
+                        std::string* err) {
+    KC_TRY(cudaMemsetAsync(dout, 0, sizeof(TierOut), st), "memset");
     if (n == 0) return KCORE_OK;
     Temp tmp(st);
     const int nb = (int)((n + kTsT - 1) / kTsT);
     uint32_t *cnt = nullptr, *off = nullptr;
-    int* bad = nullptr;
     KC_TRY(tmp.get(&cnt, (size_t)kTiers * nb), "tier counts");
     KC_TRY(tmp.get(&off, (size_t)kTiers * nb + 1), "tier offsets");
-    KC_TRY(tmp.get(&bad, 1), "flag");
-    KC_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
     if (off_bytes == 8)
-        k_tier_count<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, bad);
+        k_tier_count<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, cnt, nb,
+                                          &dout->bad);
     else
-        k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, bad);
+        k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, &dout->bad);
     count_launch();
     KC_TRY(cudaGetLastError(), "tier count");
     KC_TRY(exclusive_scan(ReadU32{cnt}, (long long)kTiers * nb, off, true, st), "tier scan");
@@ -990,18 +981,9 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
                                           init_list);
     count_launch();
     KC_TRY(cudaGetLastError(), "tier write");
-    uint32_t h[kTiers + 1];
-    int hbad = 0;
-    for (int q = 0; q <= kTiers; q++)
-        KC_TRY(cudaMemcpyAsync(&h[q], off + (long long)q * nb, sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost, st), "read tier offsets");
-    KC_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
-    if (hbad) {
-        *err = "a vertex degree is 2^30 or more";
-        return KCORE_ERR_INVALID;
-    }
-    for (int q = 0; q < kTiers; q++) tier_cnt[q] = (long long)h[q + 1] - h[q];
+    k_tier_out<<<1, 32, 0, st>>>(off, nb, row_ptr, off_bytes, n, dout);
+    count_launch();
+    KC_TRY(cudaGetLastError(), "tier out");
     return KCORE_OK;
 }
 

@@ -83,7 +83,7 @@ cudaError_t sweep_max_grid(int block, int t_lo, int t_hi, int off64, int* grid);
 
 // ---------------------------------------------------------------- CSR cleaning
 struct DevCsr {
-    int64_t n = 0, nnz = 0;
+    int64_t n = 0, nnz = 0;  // nnz = -1 until row_ptr[n] has been read back
     int off_bytes = 4;
     void* row_ptr = nullptr;
     int* col = nullptr;
@@ -102,11 +102,17 @@ kcore_status check_clean_csr(int64_t n, const void* row_ptr, int off_bytes, cons
                              int64_t nnz, cudaStream_t st, std::string* err);
 
 // Tier split: est0 = (tier << 30) | degree, and the list of all vertices with
-// tiers contiguous and ids ascending inside each tier.  tier_cnt gets the
-// sizes.
+// tiers contiguous and ids ascending inside each tier.  Enqueued only: the
+// tier boundaries, row_ptr[n] and a flag (a degree >= 2^30) land in *dout
+// (device memory) for the caller's next wait.
+struct TierOut {
+    unsigned int bound[kTiers + 1];
+    int bad;
+    long long nnz;
+};
 kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo, int t_hi,
-                        uint32_t* est0, int* init_list, long long tier_cnt[kTiers],
-                        cudaStream_t st, std::string* err);
+                        uint32_t* est0, int* init_list, TierOut* dout, cudaStream_t st,
+                        std::string* err);
 
 // Exclusive scan helper (device), out has N+1 entries when total_slot.
 cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,
@@ -119,6 +125,7 @@ long long launches();
 // Device memory from the library's stream-ordered pool (OOM reported apart
 // from other CUDA errors), and recycled small pinned host blocks.
 kcore_status dmalloc(void** p, size_t bytes, std::string* err, cudaStream_t st = 0);
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);  // free with cudaFreeAsync
 void dfree(void* p, cudaStream_t st = 0);
 constexpr size_t kPinnedBlock = 4096;
 cudaError_t pinned_get(void** p, size_t bytes);

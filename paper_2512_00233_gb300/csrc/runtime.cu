@@ -53,6 +53,13 @@ cudaError_t device_pool(cudaMemPool_t* out) {
 
 }  // namespace
 
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), pool, st);
+}
+
 kcore_status dmalloc(void** p, size_t bytes, std::string* err, cudaStream_t st) {
     *p = nullptr;
     cudaMemPool_t pool = nullptr;

@@ -376,10 +376,10 @@ kcore_status admit(kcore_batch* b) {
     int* dsl = nullptr;
     DevCsr csr;
     cudaStream_t st = b->stream;
-    cudaError_t e = cudaMallocAsync(&dsrc, sizeof(int) * std::max<long long>(samples, 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&dst_, sizeof(int) * std::max<long long>(samples, 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&dgs, sizeof(long long) * gstart.size(), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&dsl, sizeof(int) * gslot.size(), st);
+    cudaError_t e = pool_alloc((void**)&dsrc, sizeof(int) * std::max<long long>(samples, 1), st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dst_, sizeof(int) * std::max<long long>(samples, 1), st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dgs, sizeof(long long) * gstart.size(), st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dsl, sizeof(int) * gslot.size(), st);
     if (e == cudaSuccess && samples)
         e = cudaMemcpyAsync(dsrc, us.data(), sizeof(int) * samples, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && samples)
@@ -393,6 +393,12 @@ kcore_status admit(kcore_batch* b) {
     if (s == KCORE_OK) {
         s = clean_from_coo(nu, samples, dsrc, dst_, 8, st, &csr, &err);
         if (s != KCORE_OK) set_error(err);
+    }
+    if (s == KCORE_OK) {  // the cleaned size
+        e = cudaMemcpyAsync(&csr.nnz, (const long long*)csr.row_ptr + nu, sizeof(long long),
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_status(e, "batch admission size");
     }
     long long V0 = -1, E0 = -1;
     std::vector<long long> bound(gstart.size(), 0);  // union row_ptr at graph starts

@@ -43,6 +43,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "kc_common.cuh"
 
@@ -275,21 +276,25 @@ __device__ __forceinline__ int owner_of(int g, int excl) {
     return o;
 }
 
+// `valid`: u is in range (DENSE: u is a vertex id, `member` its frontier bit;
+// the row and estimate loads do not wait for the membership word).
 template <typename Off, int TW, bool DENSE>
 __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
-                                         bool valid, int u, uint32_t* hist, Acc& acc) {
+                                         bool valid, int u, const uint32_t* mword, uint32_t* hist,
+                                         Acc& acc) {
     const SweepArgs& a = *S.a;
     const int lane = threadIdx.x & 31;
     long long b = 0;
     int d = 0, k = 0;
-    uint32_t w = 0;
+    uint32_t w = 0, mw = 0xffffffffu;
+    if (DENSE) mw = __ldcg(mword);
     if (valid) {
         w = est_load(a.est + u);
         b = (long long)rp[u];
         d = (int)((long long)rp[u + 1] - b);
         k = (int)(w & kEstMask);
     }
-    if (DENSE) valid = valid && (w >> kEstBits) == 0;  // the other tiers run from their lists
+    if (DENSE) valid = valid && ((mw >> lane) & 1u) && (w >> kEstBits) == 0;  // other tiers: lists
     if (valid) {
         acc.evaluated += 1;
         acc.degsum += (unsigned)d;
@@ -390,13 +395,8 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
             if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) cand &= ~(1u << c);
 #pragma unroll
         for (int c = 0; c < kLowCache; c++)
-            word[c] = ((cand >> c) & 1u) ? __ldcg(S.bmn + (pv[c] >> 5)) : 0xffffffffu;
-#pragma unroll
-        for (int c = 0; c < kLowCache; c++) {
-            const uint32_t bit = 1u << (pv[c] & 31);
-            word[c] = (((cand >> c) & 1u) && !(word[c] & bit)) ? atomicOr(S.bmn + (pv[c] >> 5), bit)
-                                                              : 0xffffffffu;
-        }
+            word[c] = ((cand >> c) & 1u) ? atomicOr(S.bmn + (pv[c] >> 5), 1u << (pv[c] & 31))
+                                          : 0xffffffffu;
 #pragma unroll
         for (int c = 0; c < kLowCache; c++) {
             const bool fresh = ((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u);
@@ -649,13 +649,13 @@ __device__ __forceinline__ void block_barrier() { __syncthreads(); }
 template <typename Off, int T>
 __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs a) {
     __shared__ uint32_t s_hist[kHubBins];
+    __shared__ uint32_t s_lowh[kMaxBlock / 32][(T / 4) * 32];
     __shared__ uint32_t s_wsum[32];
     __shared__ unsigned long long s_acc[kAccN];
     __shared__ long long s_b[12];
     __shared__ int s_int[2];
     __shared__ uint32_t s_u32;
     __shared__ int s_wbuf[kMaxBlock / 32][kWCap];
-    __shared__ uint32_t s_lowh[kMaxBlock / 32][(T / 4) * 32];
 
     const Off* rp = (const Off*)a.row_ptr;
     SweepCtl* ctl = a.ctl;
@@ -852,25 +852,24 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
         // A large tier is walked by vertex id (dense): membership comes from the
         // bitmap word, and rows, estimates and adjacency are read coalesced.
         if (c0 > 0) {
-            if ((long long)c0 * 2 >= a.n) {
-                const unsigned nn = (unsigned)a.n;
-                const unsigned wi = 32u * max(1u, min((unsigned)a.low_chunk, nn / (32u * warps_all)));
-                run_tier(&ctl->cursor[cur][3], nn, wi, [&](unsigned i0, unsigned i1) {
+            const bool dense = (long long)c0 * 2 >= a.n;
+            const unsigned items = dense ? (unsigned)a.n : c0;
+            const unsigned wi = 32u * max(1u, min((unsigned)a.low_chunk, items / (32u * warps_all)));
+            if (dense) {
+                run_tier(&ctl->cursor[cur][3], items, wi, [&](unsigned i0, unsigned i1) {
                     for (unsigned base = i0; base < i1; base += 32u) {
-                        const uint32_t mw = __ldcg(S.bmc + (base >> 5));
                         const unsigned i = base + (unsigned)lane;
-                        const bool valid = i < i1 && ((mw >> lane) & 1u);
-                        low_warp<Off, T / 4, true>(S, Q, rp, valid, (int)i, s_lowh[wid], acc);
+                        low_warp<Off, T / 4, true>(S, Q, rp, i < i1, (int)i, S.bmc + (base >> 5),
+                                                   s_lowh[wid], acc);
                     }
                 });
             } else {
-                const unsigned wi = 32u * max(1u, min((unsigned)a.low_chunk, c0 / (32u * warps_all)));
-                run_tier(&ctl->cursor[cur][0], c0, wi, [&](unsigned i0, unsigned i1) {
+                run_tier(&ctl->cursor[cur][0], items, wi, [&](unsigned i0, unsigned i1) {
                     for (unsigned base = i0; base < i1; base += 32u) {
                         const unsigned i = base + (unsigned)lane;
                         const bool valid = i < i1;
                         const int u = valid ? list_load(S.lcur + a.tier_off[0] + i) : 0;
-                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, s_lowh[wid], acc);
+                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, nullptr, s_lowh[wid], acc);
                     }
                 });
             }
