@@ -190,6 +190,22 @@ def profiled_traffic(workload: str):
     return None
 
 
+# ---------------------------------------------------------------- ranks
+def combine_ranks(local_ms: float, units_per_rank: float, steps: int, device=None):
+    """Whole-job figures over the ranks of the default process group (or this
+    process alone): the time is the maximum over ranks, the units the sum of
+    every rank's.  Returns (max_ms, units_per_second)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = local_ms
+    if ws > 1:
+        x = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, units_per_rank * steps * ws / (t / 1e3)
+
+
 # ---------------------------------------------------------------- oracle on the host
 def oracle_pass(g):
     import oracle
@@ -323,14 +339,7 @@ def run_ours(args):
     launches = (K.lib().kcore_kernel_launches() - launches0) / args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     m = stats[0]["nnz"] // 2
-    local_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([local_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        local_ms = float(t.item())
-    total_s = local_ms / 1e3
-    value = m * args.steps * ws / total_s
+    local_ms, value = combine_ranks(sum(step_ms), m, args.steps, device=dev)
 
     # ---- decomposition alone on the resident graph (paper's timing)
     g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes)

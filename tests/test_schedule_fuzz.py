@@ -1,0 +1,102 @@
+"""Schedule fuzzer for the asynchronous activation rules (CPU only).
+
+The GPU sweep updates estimates in place while other vertices of the same
+sweep read them, so a read may return the value a neighbour had when the sweep
+began or the one it has written since.  This replays sweeps with random
+evaluation orders and random stale reads and checks the claims the kernel
+relies on (readings H4/H5):
+
+* the simple rule (push v iff new_u < x, Sec. III-B) always ends at the
+  coreness;
+* the refined rule of Sec. IV with the extra clause "or v is in the current
+  frontier" always ends at the coreness;
+* the refined rule alone (push v iff new_u < x <= old_u) does not: some
+  schedule leaves an estimate above the coreness.
+"""
+import random
+
+import numpy as np
+
+import oracle
+from tests import refimpl
+
+
+def capped_hindex(vals, cap):
+    return refimpl.hindex_sorted(vals, cap)
+
+
+def run_async(n, adj, rule, rng, max_sweeps=10_000):
+    est = [len(adj[v]) for v in range(n)]
+    frontier = set(range(n))
+    sweeps = 0
+    while frontier:
+        sweeps += 1
+        assert sweeps < max_sweeps
+        start = list(est)                     # values at the start of the sweep
+        order = list(frontier)
+        rng.shuffle(order)
+        nxt = set()
+
+        def read(v):                          # stale or fresh, at random
+            return start[v] if rng.random() < 0.5 else est[v]
+
+        for u in order:
+            k = est[u]
+            h = capped_hindex([read(v) for v in adj[u]], k)
+            if h >= k:
+                continue
+            est[u] = h
+            for v in adj[u]:
+                x = read(v)
+                if rule == "simple":
+                    push = h < x
+                elif rule == "refined_frontier":
+                    push = h < x and (x <= k or v in frontier)
+                else:                         # refined alone
+                    push = h < x and x <= k
+                if push:
+                    nxt.add(v)
+        frontier = nxt
+    return est
+
+
+def random_graph(rng, n, p):
+    adj = [set() for _ in range(n)]
+    for a in range(n):
+        for b in range(a + 1, n):
+            if rng.random() < p:
+                adj[a].add(b)
+                adj[b].add(a)
+    return [sorted(s) for s in adj]
+
+
+def coreness(n, adj):
+    src = [a for a in range(n) for b in adj[a]]
+    dst = [b for a in range(n) for b in adj[a]]
+    rp, col = oracle.csr_build(n, np.array(src, np.int32), np.array(dst, np.int32))
+    return oracle.coreness(n, rp, col).tolist()
+
+
+def test_safe_rules_always_reach_the_coreness():
+    rng = random.Random(2024)
+    for trial in range(250):
+        n = rng.randint(2, 24)
+        adj = random_graph(rng, n, rng.uniform(0.1, 0.6))
+        core = coreness(n, adj)
+        for rule in ("simple", "refined_frontier"):
+            for _ in range(3):
+                assert run_async(n, adj, rule, rng) == core, (trial, rule)
+
+
+def test_refined_rule_alone_can_fail_in_place():
+    rng = random.Random(7)
+    failures = 0
+    for trial in range(400):
+        n = rng.randint(4, 20)
+        adj = random_graph(rng, n, rng.uniform(0.2, 0.6))
+        core = coreness(n, adj)
+        for _ in range(4):
+            est = run_async(n, adj, "refined_alone", rng)
+            assert all(e >= c for e, c in zip(est, core))   # never below the coreness
+            failures += est != core
+    assert failures > 0
