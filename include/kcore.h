@@ -62,6 +62,11 @@ typedef int32_t kcore_status;
                                         read of est(v) may be stale)                  */
 #define KCORE_ASYNC       (1u << 5)  /* kcore_run returns once the work is enqueued;
                                         kcore_wait() reports the status               */
+#define KCORE_GRAPH       (1u << 6)  /* kcore_run: capture the run (initialisation, the
+                                        persistent sweep launch, output) into a CUDA
+                                        graph on first use and replay it afterwards;
+                                        needs KCORE_OUT_DEVICE.  Re-captured when the
+                                        output pointer, mode flags or options change  */
 
 /* ---- options ------------------------------------------------------------ */
 /*
@@ -133,7 +138,8 @@ kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const 
  * kcore_run -- compute the coreness of every vertex.
  *   coreness_out  n int32 values, caller-owned; a host pointer, or a device
  *                 pointer with KCORE_OUT_DEVICE.
- *   flags         KCORE_OUT_DEVICE, KCORE_SYNC_MODE, KCORE_REFINED, KCORE_ASYNC.
+ *   flags         KCORE_OUT_DEVICE, KCORE_SYNC_MODE, KCORE_REFINED, KCORE_ASYNC,
+ *                 KCORE_GRAPH.
  * Each run starts from est = degree (Alg. 1 initialisation) and iterates on the
  * device until no vertex is active; one persistent kernel runs every sweep.
  * Without KCORE_ASYNC the call waits for the result and returns its status;

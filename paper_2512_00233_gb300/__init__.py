@@ -11,7 +11,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (KCORE_ASYNC, KCORE_ERR_AGAIN, KCORE_ERR_CANCELLED, KCORE_ERR_INVALID,
+from ._lib import (KCORE_ASYNC, KCORE_GRAPH, KCORE_ERR_AGAIN, KCORE_ERR_CANCELLED, KCORE_ERR_INVALID,
                    KCORE_ERR_NOT_CONVERGED, KCORE_ERR_TIMEOUT, KCORE_IN_CLEAN, KCORE_IN_DEVICE,
                    KCORE_OK, KCORE_OUT_DEVICE, KCORE_PENDING, KCORE_REFINED, KCORE_SYNC_MODE,
                    SIGNATURES, BatchStats, KCoreError, Options, RunStats, ServeOptions, check, lib)
@@ -121,7 +121,7 @@ class Graph:
 
     # ---------------------------------------------------------------- run
     def run(self, out=None, device: bool = True, sync_mode: bool = False, refined: bool = False,
-            wait: bool = True, stream=None, check_status: bool = True):
+            wait: bool = True, stream=None, check_status: bool = True, graph: bool = False):
         """Coreness of every vertex.  Returns `out` (allocated when None: an
         int32 CUDA tensor if device else a numpy array)."""
         if out is None:
@@ -133,7 +133,8 @@ class Graph:
         is_dev = _is_cuda_tensor(out)
         ptr = out.data_ptr() if is_dev else out.ctypes.data
         flags = (KCORE_OUT_DEVICE if is_dev else 0) | (KCORE_SYNC_MODE if sync_mode else 0) | \
-            (KCORE_REFINED if refined else 0) | (0 if wait else KCORE_ASYNC)
+            (KCORE_REFINED if refined else 0) | (0 if wait else KCORE_ASYNC) | \
+            (KCORE_GRAPH if graph else 0)
         st = lib().kcore_run(self._h, ptr, flags, _stream(stream))
         if check_status:
             check(st, "kcore_run")
@@ -165,6 +166,12 @@ class Graph:
         if with_time:
             return f[:k], d[:k], u[:k], t[:k]
         return f[:k], d[:k], u[:k]
+
+    def row_ptr_host(self):
+        """row_ptr of the cleaned graph as a numpy array."""
+        rp = np.empty(self.n + 1, dtype=np.int64 if self.row_ptr_bytes == 8 else np.int32)
+        check(lib().kcore_copy_csr(self._h, rp.ctypes.data, None, 0), "kcore_copy_csr")
+        return rp
 
     def csr(self):
         """(row_ptr, col_idx) of the cleaned graph, as numpy arrays."""

@@ -31,6 +31,7 @@ KCORE_OUT_DEVICE = 1 << 2
 KCORE_SYNC_MODE = 1 << 3
 KCORE_REFINED = 1 << 4
 KCORE_ASYNC = 1 << 5
+KCORE_GRAPH = 1 << 6
 
 KCORE_NOALLOC_MAX_N = 1 << 19
 

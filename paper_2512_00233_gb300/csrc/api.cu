@@ -88,6 +88,14 @@ struct kcore_graph {
     kcore_status last_status = KCORE_OK;
     int last_grid = 0;
     float ms_create = 0.f;
+    // KCORE_GRAPH: captured run
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t join[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec = nullptr;
+    int32_t* gout = nullptr;
+    uint32_t gflags = 0;
+    long long gopt_epoch = -1, opt_epoch = 0;
+    long long gkernels = 0;   // kernels in the captured graph
 };
 
 namespace {
@@ -117,6 +125,10 @@ void release(kcore_graph* g) {
     if (g->hctl) pinned_put(g->hctl);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    for (auto& e : g->join)
+        if (e) cudaEventDestroy(e);
+    if (g->gstream) cudaStreamDestroy(g->gstream);
     cudaSetDevice(prev);
     delete g;
 }
@@ -396,6 +408,7 @@ kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* c
     (void)s;
     const bool rebin = o.t_lo != g->opt.t_lo || o.t_hi != g->opt.t_hi;
     g->opt = o;
+    g->opt_epoch++;
     if (!rebin) return KCORE_OK;
     std::string err;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -405,21 +418,20 @@ kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* c
     return read_tiers(g, st);
 }
 
-kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, void* cuda_stream) {
-    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+// Enqueues one run on `st` (no wait).  The sequence is the same whether it
+// runs directly or is captured into a CUDA graph.
+// Under capture the events become event-record nodes of the graph, so the
+// timings and the completion event work the same way on replay.
+cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
+    return cudaEventRecordWithFlags(ev, st, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, cudaStream_t st,
+                         bool capture) {
     const int64_t n = g->csr.n;
-    if (n > 0 && !coreness_out) return fail(KCORE_ERR_INVALID, "coreness_out is NULL");
-    if (g->pending) wait_run(g);
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool sync_mode = (flags & KCORE_SYNC_MODE) != 0;
-    std::string err;
-    if (sync_mode && !g->upd_list) {
-        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
-        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
-        if (s != KCORE_OK) return fail(s, err);
-    }
     const size_t words = (size_t)((n + 31) / 32);
-    cudaError_t e = cudaEventRecord(g->ev[EV_R0], st);
+    cudaError_t e = record(g->ev[EV_R0], st, capture);
     if (e == cudaSuccess && n)
         e = cudaMemcpyAsync(g->est, g->est0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[0], 0xff, sizeof(uint32_t) * words, st);
@@ -466,11 +478,11 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
     long long want = (work + (long long)g->opt.block * 32 - 1) / ((long long)g->opt.block * 32);
     want = std::max<long long>(1, want);
     if (g->opt.max_ctas > 0) want = std::min<long long>(want, g->opt.max_ctas);
-    e = cudaEventRecord(g->ev[EV_S0], st);
+    e = record(g->ev[EV_S0], st, capture);
     if (e == cudaSuccess)
         e = launch_sweep(a, g->opt.block, (int)std::min<long long>(want, INT_MAX), g->opt.ctas_per_sm,
                          st, &g->last_grid);
-    if (e == cudaSuccess) e = cudaEventRecord(g->ev[EV_S1], st);
+    if (e == cudaSuccess) e = record(g->ev[EV_S1], st, capture);
     if (e != cudaSuccess) return cuda_status(e, "sweep launch");
     if (flags & KCORE_OUT_DEVICE) {
         e = launch_output(g->est, coreness_out, n, st);
@@ -481,8 +493,73 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->hctl, g->ctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaEventRecord(g->ev[EV_R1], st);
+    if (e == cudaSuccess) e = record(g->ev[EV_R1], st, capture);
     if (e != cudaSuccess) return cuda_status(e, "kcore_run output");
+    return KCORE_OK;
+}
+
+// KCORE_GRAPH: the run's sequence is captured once on the graph's own stream
+// and replayed; the caller's stream and that stream are joined by events.
+kcore_status graph_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, cudaStream_t st) {
+    const uint32_t key_flags = flags & (KCORE_SYNC_MODE | KCORE_REFINED);
+    cudaError_t e = cudaSuccess;
+    if (!g->gstream) {
+        e = cudaStreamCreateWithFlags(&g->gstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join[1], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_status(e, "graph stream");
+    }
+    if (!g->gexec || g->gout != coreness_out || g->gflags != key_flags || g->gopt_epoch != g->opt_epoch) {
+        if (g->gexec) cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(g->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_status(e, "begin capture");
+        const long long before = g_launches.load();
+        kcore_status s = enqueue_run(g, coreness_out, key_flags | KCORE_OUT_DEVICE, g->gstream, true);
+        e = cudaStreamEndCapture(g->gstream, &graph);
+        g->gkernels = g_launches.load() - before;
+        g_launches.fetch_sub(g->gkernels);   // counted again at each replay
+        if (s != KCORE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "end capture");
+        e = cudaGraphInstantiate(&g->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_status(e, "graph instantiate");
+        g->gout = coreness_out;
+        g->gflags = key_flags;
+        g->gopt_epoch = g->opt_epoch;
+    }
+    e = cudaEventRecord(g->join[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->gstream, g->join[0], 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g->gexec, g->gstream);
+    if (e == cudaSuccess) g_launches.fetch_add(g->gkernels);
+    if (e == cudaSuccess) e = cudaEventRecord(g->join[1], g->gstream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->join[1], 0);
+    if (e != cudaSuccess) return cuda_status(e, "graph launch");
+    return KCORE_OK;
+}
+
+kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, void* cuda_stream) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    const int64_t n = g->csr.n;
+    if (n > 0 && !coreness_out) return fail(KCORE_ERR_INVALID, "coreness_out is NULL");
+    if ((flags & KCORE_GRAPH) && !(flags & KCORE_OUT_DEVICE))
+        return fail(KCORE_ERR_INVALID, "KCORE_GRAPH needs a device output (KCORE_OUT_DEVICE)");
+    if (g->pending) wait_run(g);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::string err;
+    if ((flags & KCORE_SYNC_MODE) && !g->upd_list) {
+        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
+        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
+        if (s == KCORE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = KCORE_ERR_CUDA;
+        if (s != KCORE_OK) return fail(s, err);
+    }
+    kcore_status s = (flags & KCORE_GRAPH) ? graph_run(g, coreness_out, flags, st)
+                                          : enqueue_run(g, coreness_out, flags, st, false);
+    if (s != KCORE_OK) return s;
     g->pending = true;
     g->ran = true;
     if (flags & KCORE_ASYNC) return KCORE_OK;
