@@ -55,11 +55,10 @@ typedef int32_t kcore_status;
 #define KCORE_SYNC_MODE   (1u << 3)  /* synchronous rounds (Alg. 3): every round reads a
                                         snapshot of the estimates; deterministic per
                                         round.  Default: in-place asynchronous sweeps */
-#define KCORE_REFINED     (1u << 4)  /* refined activation (Sec. IV, Further
-                                        Optimizations): u re-activates v only if
-                                        new_u < est(v) <= old_u; in asynchronous mode
-                                        also when v is in the current frontier (its
-                                        read of est(v) may be stale)                  */
+#define KCORE_REFINED     (1u << 4)  /* synchronous mode: refined activation (Sec. IV,
+                                        Further Optimizations): u re-activates v only
+                                        if new_u < est(v) <= old_u.  Asynchronous
+                                        mode uses it by default (see KCORE_SIMPLE)    */
 #define KCORE_ASYNC       (1u << 5)  /* kcore_run returns once the work is enqueued;
                                         kcore_wait() reports the status               */
 #define KCORE_GRAPH       (1u << 6)  /* kcore_run: capture the run (initialisation, the
@@ -67,19 +66,30 @@ typedef int32_t kcore_status;
                                         graph on first use and replay it afterwards;
                                         needs KCORE_OUT_DEVICE.  Re-captured when the
                                         output pointer, mode flags or options change  */
+#define KCORE_SIMPLE      (1u << 7)  /* asynchronous mode: the simple activation rule
+                                        of Sec. III-B (v re-activated whenever
+                                        new_u < est(v)).  Without it, asynchronous
+                                        sweeps use the refined rule, kept exact under
+                                        in-place updates: while v may still be
+                                        evaluating in the same sweep, the simple rule
+                                        applies to it; once v is done, its final
+                                        estimate decides new_u < est(v) <= old_u.
+                                        Both give the coreness; they differ in the
+                                        work done                                      */
 
 /* ---- options ------------------------------------------------------------ */
 /*
  * Tuning knobs of the sweep engine.  Fill with kcore_default_options() and
  * override fields; 0 in a field means "library default".  The degree tiers
  * split the frontier by degree d: d <= t_lo is evaluated by one thread with a
- * register histogram, t_lo < d <= t_hi by one warp, d > t_hi by one CTA with a
- * shared-memory histogram.
+ * register histogram, t_lo < d <= t_hi by one warp (estimates in registers up
+ * to degree 256, staged in shared memory above), d > t_hi by one CTA with
+ * shared-memory counters.
  */
 typedef struct kcore_options {
     uint32_t struct_size;   /* sizeof(kcore_options)                                */
     int32_t  t_lo;          /* thread-tier degree bound, 1..16 (default 16)          */
-    int32_t  t_hi;          /* warp-tier degree bound, t_lo..256 (default 256)       */
+    int32_t  t_hi;          /* warp-tier degree bound, t_lo..2048 (default 2048)     */
     int32_t  block;         /* threads per CTA of the sweep kernel, 64..512, x32     */
     int32_t  low_chunk;     /* thread tier: vertices per lane per work grab (1..8)   */
     int32_t  med_chunk;     /* warp tier: vertices per warp per work grab (1..64)    */
@@ -138,8 +148,8 @@ kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const 
  * kcore_run -- compute the coreness of every vertex.
  *   coreness_out  n int32 values, caller-owned; a host pointer, or a device
  *                 pointer with KCORE_OUT_DEVICE.
- *   flags         KCORE_OUT_DEVICE, KCORE_SYNC_MODE, KCORE_REFINED, KCORE_ASYNC,
- *                 KCORE_GRAPH.
+ *   flags         KCORE_OUT_DEVICE, KCORE_SYNC_MODE, KCORE_REFINED, KCORE_SIMPLE,
+ *                 KCORE_ASYNC, KCORE_GRAPH.
  * Each run starts from est = degree (Alg. 1 initialisation) and iterates on the
  * device until no vertex is active; one persistent kernel runs every sweep.
  * Without KCORE_ASYNC the call waits for the result and returns its status;
@@ -177,8 +187,10 @@ kcore_status kcore_copy_csr(const kcore_graph* g, void* row_ptr_out, int32_t* co
  * Statistics of the last run (synchronises with it).  Per-sweep counts follow
  * Fig. 5 (activated vertices per iteration); bytes_algorithmic is what the
  * method must move for the vertices it evaluated: per evaluated vertex u,
- * 2 row_ptr entries + est[u] + deg(u) col_idx entries + deg(u) estimate
- * gathers, plus 4 bytes per update.
+ * 2 row_ptr entries + est[u], then one col_idx entry and one estimate gather
+ * per adjacency entry read (entries_read: deg(u), or fewer when the
+ * no-change test of a high-degree vertex found est[u] supporters early),
+ * plus 4 bytes per update.
  */
 typedef struct kcore_run_stats {
     int64_t n, nnz;             /* graph size (nnz = 2m)                              */
@@ -196,6 +208,8 @@ typedef struct kcore_run_stats {
     float   ms_create;          /* kcore_create device time (cleaning)                 */
     float   ms_sweep;           /* sweep kernel device time                            */
     float   ms_run;             /* whole kcore_run device time (init..output)          */
+    int64_t entries_read;       /* adjacency entries read to evaluate (<= edges_scanned) */
+    int64_t decrease;           /* sum over updates of (old - new) estimate              */
 } kcore_run_stats;
 
 kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out);
@@ -208,6 +222,18 @@ kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out);
  */
 kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsum,
                                int64_t* updates, int64_t* start_ns, int64_t cap, int64_t* count);
+
+/*
+ * Further per-sweep columns of the same trace: adjacency entries read to
+ * evaluate the frontier (below its degree sum where the no-change test stopped
+ * early) and the sum of the estimate decreases made in the sweep.  Estimates
+ * start at the degree and never go below the coreness, so after sweep s
+ *   sum_v |est_v - core_v| = sum_v deg_v - sum_{s' <= s} decrease[s'] - sum_v core_v,
+ * the convergence error of Fig. 4, without copying estimates out.
+ * Same conventions as kcore_sweep_trace.
+ */
+kcore_status kcore_sweep_detail(kcore_graph* g, int64_t* entries_read, int64_t* decrease,
+                                int64_t cap, int64_t* count);
 
 /* Release a graph (waits for its outstanding work).  NULL is ignored. */
 void kcore_destroy(kcore_graph* g);

@@ -11,7 +11,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (KCORE_ASYNC, KCORE_GRAPH, KCORE_ERR_AGAIN, KCORE_ERR_CANCELLED, KCORE_ERR_INVALID,
+from ._lib import (KCORE_ASYNC, KCORE_GRAPH, KCORE_SIMPLE, KCORE_ERR_AGAIN, KCORE_ERR_CANCELLED, KCORE_ERR_INVALID,
                    KCORE_ERR_NOT_CONVERGED, KCORE_ERR_TIMEOUT, KCORE_IN_CLEAN, KCORE_IN_DEVICE,
                    KCORE_OK, KCORE_OUT_DEVICE, KCORE_PENDING, KCORE_REFINED, KCORE_SYNC_MODE,
                    SIGNATURES, BatchStats, KCoreError, Options, RunStats, ServeOptions, check, lib)
@@ -120,10 +120,14 @@ class Graph:
         return cls(h.value)
 
     # ---------------------------------------------------------------- run
-    def run(self, out=None, device: bool = True, sync_mode: bool = False, refined: bool = False,
+    def run(self, out=None, device: bool = True, sync_mode: bool = False, refined: bool | None = None,
             wait: bool = True, stream=None, check_status: bool = True, graph: bool = False):
         """Coreness of every vertex.  Returns `out` (allocated when None: an
-        int32 CUDA tensor if device else a numpy array)."""
+        int32 CUDA tensor if device else a numpy array).  `refined`: activation
+        rule; None = the library default (refined when asynchronous, the
+        simple rule of Alg. 3 when synchronous)."""
+        if refined is None:
+            refined = not sync_mode
         if out is None:
             if device:
                 torch = _torch()
@@ -133,7 +137,8 @@ class Graph:
         is_dev = _is_cuda_tensor(out)
         ptr = out.data_ptr() if is_dev else out.ctypes.data
         flags = (KCORE_OUT_DEVICE if is_dev else 0) | (KCORE_SYNC_MODE if sync_mode else 0) | \
-            (KCORE_REFINED if refined else 0) | (0 if wait else KCORE_ASYNC) | \
+            (KCORE_REFINED if refined and sync_mode else 0) | \
+            (KCORE_SIMPLE if not refined and not sync_mode else 0) | (0 if wait else KCORE_ASYNC) | \
             (KCORE_GRAPH if graph else 0)
         st = lib().kcore_run(self._h, ptr, flags, _stream(stream))
         if check_status:
@@ -166,6 +171,15 @@ class Graph:
         if with_time:
             return f[:k], d[:k], u[:k], t[:k]
         return f[:k], d[:k], u[:k]
+
+    def trace_detail(self, cap: int = 1 << 16):
+        """Per-sweep (adjacency entries read, sum of estimate decreases)."""
+        r = np.zeros(cap, np.int64)
+        dec = np.zeros(cap, np.int64)
+        cnt = ctypes.c_int64()
+        check(lib().kcore_sweep_detail(self._h, r.ctypes.data, dec.ctypes.data, cap,
+                                       ctypes.byref(cnt)), "kcore_sweep_detail")
+        return r[:cnt.value], dec[:cnt.value]
 
     def row_ptr_host(self):
         """row_ptr of the cleaned graph as a numpy array."""

@@ -32,6 +32,7 @@ KCORE_SYNC_MODE = 1 << 3
 KCORE_REFINED = 1 << 4
 KCORE_ASYNC = 1 << 5
 KCORE_GRAPH = 1 << 6
+KCORE_SIMPLE = 1 << 7
 
 KCORE_NOALLOC_MAX_N = 1 << 19
 
@@ -56,7 +57,7 @@ class RunStats(ctypes.Structure):
                 ("pushes", c_i64), ("bytes_algorithmic", c_i64), ("status", c_i32),
                 ("grid", c_i32), ("block", c_i32), ("row_ptr_bytes", c_i32),
                 ("ms_create", ctypes.c_float), ("ms_sweep", ctypes.c_float),
-                ("ms_run", ctypes.c_float)]
+                ("ms_run", ctypes.c_float), ("entries_read", c_i64), ("decrease", c_i64)]
 
 
 class ServeOptions(ctypes.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "kcore_copy_csr": (c_i32, [c_vp, c_vp, c_vp, c_u32]),
     "kcore_stats": (c_i32, [c_vp, ctypes.POINTER(RunStats)]),
     "kcore_sweep_trace": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
+    "kcore_sweep_detail": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "kcore_destroy": (None, [c_vp]),
     "kcore_run_noalloc": (c_i32, [c_i64, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "kcore_default_serve_options": (None, [ctypes.POINTER(ServeOptions)]),

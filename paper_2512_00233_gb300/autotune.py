@@ -24,7 +24,7 @@ from . import Graph, Options, default_options
 
 SPACE = {
     "t_lo": [4, 8, 16],
-    "t_hi": [32, 64, 128, 256],
+    "t_hi": [64, 256, 512, 1024, 2048],
     "block": [256, 512],
     "low_chunk": [2, 4, 8],
     "med_chunk": [1, 4, 16],

@@ -6,6 +6,7 @@
 #include <climits>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "kc_common.cuh"
 
@@ -48,8 +49,8 @@ kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
     if (in->max_sweeps) out->max_sweeps = in->max_sweeps;
     if (in->timeout_s > 0) out->timeout_s = in->timeout_s;
     if (out->t_lo < 1 || out->t_lo > 32) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..32");
-    if (out->t_hi < out->t_lo || out->t_hi > 256)
-        return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..256");
+    if (out->t_hi < out->t_lo || out->t_hi > kMedBig)
+        return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..2048");
     if (out->t_lo > 16) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..16");
     if (out->block < 64 || out->block > 512 || out->block % 32)
         return fail(KCORE_ERR_INVALID, "block must be a multiple of 32 in 64..512");
@@ -171,7 +172,7 @@ kcore_status finish_graph(kcore_graph* g, cudaStream_t st) {
     }
     KC_ALLOC(g->ctl, sizeof(SweepCtl));
     g->max_trace = 1 << 16;
-    KC_ALLOC(g->trace, sizeof(long long) * 4 * g->max_trace);
+    KC_ALLOC(g->trace, sizeof(long long) * kTraceCols * g->max_trace);
     KC_ALLOC(g->dtier, sizeof(TierOut));
 #undef KC_ALLOC
     static_assert(sizeof(SweepCtl) <= 2048 && sizeof(TierOut) <= kPinnedBlock - 2048,
@@ -257,7 +258,7 @@ void kcore_default_options(kcore_options* o) {
     memset(o, 0, sizeof(*o));
     o->struct_size = sizeof(kcore_options);
     o->t_lo = 16;
-    o->t_hi = 256;
+    o->t_hi = 2048;
     o->block = 512;
     o->low_chunk = 8;
     o->med_chunk = 4;
@@ -470,7 +471,9 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
     a.med_chunk = g->opt.med_chunk;
     a.tail_max = g->opt.tail_max < 0 ? 0 : g->opt.tail_max;
     a.sync_mode = sync_mode ? 1 : 0;
-    a.refined = (flags & KCORE_REFINED) ? 1 : 0;
+    // synchronous: Alg. 3 as printed unless KCORE_REFINED; asynchronous: the
+    // refined rule unless KCORE_SIMPLE
+    a.refined = sync_mode ? ((flags & KCORE_REFINED) ? 1 : 0) : ((flags & KCORE_SIMPLE) ? 0 : 1);
     a.off64 = g->csr.off_bytes == 8 ? 1 : 0;
 
     // Grid: enough CTAs for the first sweep's work, at most the co-resident maximum.
@@ -501,7 +504,7 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
 // KCORE_GRAPH: the run's sequence is captured once on the graph's own stream
 // and replayed; the caller's stream and that stream are joined by events.
 kcore_status graph_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, cudaStream_t st) {
-    const uint32_t key_flags = flags & (KCORE_SYNC_MODE | KCORE_REFINED);
+    const uint32_t key_flags = flags & (KCORE_SYNC_MODE | KCORE_REFINED | KCORE_SIMPLE);
     cudaError_t e = cudaSuccess;
     if (!g->gstream) {
         e = cudaStreamCreateWithFlags(&g->gstream, cudaStreamNonBlocking);
@@ -612,11 +615,29 @@ kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out) {
     out->edges_scanned = (int64_t)c.tot[kAccDegsum];
     out->updates = (int64_t)c.tot[kAccUpdates];
     out->pushes = (int64_t)c.tot[kAccPushes];
+    out->entries_read = (int64_t)(c.tot[kAccDegsum] - c.tot[kAccSkipped]);
+    out->decrease = (int64_t)c.tot[kAccDec];
     out->bytes_algorithmic = out->evaluated * (2LL * g->csr.off_bytes + 4) +
-                             8LL * out->edges_scanned + 4LL * out->updates;
+                             8LL * out->entries_read + 4LL * out->updates;
     out->grid = g->last_grid;
     cudaEventElapsedTime(&out->ms_sweep, g->ev[EV_S0], g->ev[EV_S1]);
     cudaEventElapsedTime(&out->ms_run, g->ev[EV_R0], g->ev[EV_R1]);
+    return KCORE_OK;
+}
+
+// Copies the first min(cap, recorded) rows of the device trace to the host.
+static kcore_status trace_rows(kcore_graph* g, int64_t cap, std::vector<long long>* rows,
+                               long long* count) {
+    *count = 0;
+    if (!g->ran) return KCORE_OK;
+    wait_run(g);
+    const long long n = std::min<long long>({(long long)cap, g->hctl->sweep, g->max_trace});
+    if (n <= 0) return KCORE_OK;
+    rows->resize((size_t)(kTraceCols * n));
+    cudaError_t e = cudaMemcpy(rows->data(), g->trace, sizeof(long long) * kTraceCols * n,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e, "kcore_sweep_trace");
+    *count = n;
     return KCORE_OK;
 }
 
@@ -624,23 +645,34 @@ kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsu
                                int64_t* updates, int64_t* start_ns, int64_t cap, int64_t* count) {
     if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
     if (count) *count = 0;
-    if (!g->ran) return KCORE_OK;
-    wait_run(g);
-    const long long n = std::min<long long>({(long long)cap, g->hctl->sweep, g->max_trace});
-    if (n <= 0) return KCORE_OK;
-    long long* h = new long long[4 * n];
-    cudaError_t e = cudaMemcpy(h, g->trace, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-        delete[] h;
-        return cuda_status(e, "kcore_sweep_trace");
-    }
+    std::vector<long long> h;
+    long long n = 0;
+    kcore_status s = trace_rows(g, cap, &h, &n);
+    if (s != KCORE_OK) return s;
     for (long long i = 0; i < n; i++) {
-        if (frontier) frontier[i] = h[4 * i];
-        if (degsum) degsum[i] = h[4 * i + 1];
-        if (updates) updates[i] = h[4 * i + 2];
-        if (start_ns) start_ns[i] = h[4 * i + 3] - h[3];
+        const long long* r = h.data() + kTraceCols * i;
+        if (frontier) frontier[i] = r[kTrFrontier];
+        if (degsum) degsum[i] = r[kTrDegsum];
+        if (updates) updates[i] = r[kTrUpdates];
+        if (start_ns) start_ns[i] = r[kTrStart] - h[kTrStart];
     }
-    delete[] h;
+    if (count) *count = n;
+    return KCORE_OK;
+}
+
+kcore_status kcore_sweep_detail(kcore_graph* g, int64_t* entries_read, int64_t* decrease,
+                                int64_t cap, int64_t* count) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    if (count) *count = 0;
+    std::vector<long long> h;
+    long long n = 0;
+    kcore_status s = trace_rows(g, cap, &h, &n);
+    if (s != KCORE_OK) return s;
+    for (long long i = 0; i < n; i++) {
+        const long long* r = h.data() + kTraceCols * i;
+        if (entries_read) entries_read[i] = r[kTrRead];
+        if (decrease) decrease[i] = r[kTrDec];
+    }
     if (count) *count = n;
     return KCORE_OK;
 }

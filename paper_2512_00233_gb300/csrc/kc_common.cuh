@@ -17,10 +17,21 @@ namespace kc {
 constexpr uint32_t kEstBits = 30;
 constexpr uint32_t kEstMask = (1u << kEstBits) - 1u;
 constexpr int kTiers = 3;
+constexpr int kMedBig = 2048;      // largest degree of the warp tier (t_hi <= kMedBig)
 constexpr int kHubBins = 4096;   // shared-memory histogram of the CTA tier
 
 // Accumulator indices of per-sweep statistics.
-enum { kAccEvaluated = 0, kAccDegsum = 1, kAccUpdates = 2, kAccPushes = 3, kAccN = 4 };
+enum {
+    kAccEvaluated = 0,
+    kAccDegsum = 1,   // frontier degree sum
+    kAccUpdates = 2,
+    kAccPushes = 3,
+    kAccSkipped = 4,  // adjacency entries not read thanks to an early exit
+    kAccDec = 5,      // sum of estimate decreases
+    kAccN = 6
+};
+// Columns of the per-sweep trace.
+enum { kTrFrontier = 0, kTrDegsum, kTrUpdates, kTrStart, kTrRead, kTrDec, kTraceCols };
 
 // Control block of the persistent sweep kernel (device memory).  Counter slot
 // s % 4 holds the frontier counts of sweep s; sweep s pushes into slot

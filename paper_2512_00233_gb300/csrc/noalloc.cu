@@ -172,6 +172,7 @@ extern "C" kcore_status kcore_run_noalloc(int64_t n, const void* row_ptr, int32_
 
     SweepArgs a;
     memset(&a, 0, sizeof(a));
+    a.refined = 1;  // asynchronous sweeps: the refined activation rule
     a.row_ptr = row_ptr;
     a.col = col_idx;
     a.est = est;

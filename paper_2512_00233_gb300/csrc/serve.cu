@@ -467,6 +467,7 @@ kcore_status admit(kcore_batch* b) {
 kcore_status run_chunk(kcore_batch* b) {
     SweepArgs a;
     memset(&a, 0, sizeof(a));
+    a.refined = 1;  // asynchronous sweeps: the refined activation rule
     a.row_ptr = b->rp;
     a.col = b->col;
     a.est = b->est;

@@ -12,13 +12,20 @@
 // Activation (u lowered from k to h, x = the value of est[v] that u reads):
 //   simple  (selective sending, Sec. III-B):          push v iff h < x.
 //   refined (Sec. IV, Further Optimizations):         push v iff h < x and
-//           (x <= k  or  v is in F_s).
-// Only v writes est[v], and only while it is evaluated, so for v outside F_s
-// the value u reads is exact and FastK's condition x <= old_u applies as is;
-// for v inside F_s the read may be stale and the simple rule is used.  Either
-// way every vertex whose support u withdraws is re-evaluated; a stale read can
-// only over-activate.  (The plain refined condition without the F_s clause is
+//           (x <= k  or  v may still be evaluating in this sweep).
+// Only v writes est[v], and only while it is evaluated.  A vertex of F_s
+// clears its own membership bit once its evaluation is over (after a fence
+// that orders its estimate store first).  When u finds v's bit clear (v is
+// done, or was never in F_s), it reads est[v] again, after a fence, and
+// applies FastK's condition h < x <= k to that value: v's final value of the
+// sweep.  If it exceeds k, v's h-index never counted u (u's value was at most
+// k), so u's decrease cannot lower it.  When v's bit is still set, v may be
+// reading u's old value right now, and the simple rule applies.  Either way
+// every vertex whose support u withdraws is re-evaluated; a stale read can
+// only over-activate.  (The plain refined condition, with no second read, is
 // unsafe with in-place updates: v may lower concurrently using u's old value.)
+// Membership bits are cleared only for the warp and CTA tiers, whose
+// re-evaluation is expensive; a set bit is always safe.
 //
 // Degree tiers (est word bits 30-31): d <= t_lo one thread per vertex, its
 // neighbour ids and estimates in registers and a byte-packed register
@@ -74,8 +81,12 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long* p)
 __device__ __forceinline__ uint32_t est_load(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ int list_load(const int* p) { return __ldcg(p); }
 
+
 struct Acc {
-    unsigned long long evaluated, degsum, updates, pushes;
+    unsigned evaluated, updates, pushes;
+    unsigned long long degsum;   // frontier degree sum
+    unsigned long long skipped;  // adjacency entries an early exit did not read
+    unsigned long long dec;      // sum of estimate decreases
 };
 
 // Per-warp push buffers: each warp collects its pushes in its own slice of
@@ -94,6 +105,8 @@ struct Sweep {
     const int* lcur;
     int* lnxt;
     const uint32_t* bmc;   // F_s membership
+    uint32_t* bmc_w;       // the same bitmap, for clearing finished vertices
+    bool mark;             // clear the bits of finished warp / CTA tier vertices
     uint32_t* bmn;         // F_{s+1} membership
     int* wbuf;             // shared: this warp's push buffer (kWCap entries)
 };
@@ -107,11 +120,21 @@ __device__ __forceinline__ bool in_current(const Sweep& S, int v) {
     return (__ldcg(S.bmc + (v >> 5)) >> (v & 31)) & 1u;
 }
 
-// Activation rule for a neighbour v read as x while u goes from k to h.
-__device__ __forceinline__ bool should_push(const Sweep& S, int h, int k, int x, int v) {
-    if (x <= h) return false;
-    if (!S.a->refined || x <= k) return true;
-    return in_current(S, v);
+// Refined rule for a neighbour v read as x > k while u goes from k to h:
+// keep v if it may still be evaluating (bit set); otherwise decide on its
+// final value, read after the bit.
+__device__ __forceinline__ bool refined_keep(const Sweep& S, int h, int k, int v) {
+    if (in_current(S, v)) return true;
+    __threadfence();
+    const int x2 = (int)(est_load(S.a->est + v) & kEstMask);
+    return h < x2 && x2 <= k;
+}
+
+// Marks u's evaluation in sweep s as over (warp and CTA tiers, refined
+// asynchronous mode): after its estimate store, clears its F_s bit.
+__device__ __forceinline__ void mark_done(const Sweep& S, int u, bool wrote) {
+    if (wrote) __threadfence();
+    atomicAnd(S.bmc_w + (u >> 5), ~(1u << (u & 31)));
 }
 
 // Appends the warp's buffered pushes of tier q to the global list.  All 32
@@ -132,6 +155,43 @@ __device__ __forceinline__ void warp_flush(const Sweep& S, WarpQ& Q, int q) {
 __device__ __forceinline__ void warp_flush_all(const Sweep& S, WarpQ& Q) {
 #pragma unroll
     for (int q = 0; q < kTiers; q++) warp_flush(S, Q, q);
+}
+
+// End-of-sweep flush of every warp's push buffers with one global atomic per
+// tier per CTA (instead of one per warp: thousands of warps adding to the same
+// three counters serialise on them).  All threads of the CTA call.
+// s_cnt: 3 * 32 words of shared memory.
+__device__ __forceinline__ void cta_flush_all(const Sweep& S, WarpQ& Q, uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < kTiers; q++) s_cnt[q * 32 + wid] = Q.n[q];
+    __syncthreads();
+    if (wid == 0) {
+        for (int q = 0; q < kTiers; q++) {
+            const unsigned c = lane < nw ? s_cnt[q * 32 + lane] : 0u;
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const unsigned total = __shfl_sync(kFull, incl, 31);
+            unsigned base = 0;
+            if (lane == 0 && total) base = atomicAdd(&S.a->ctl->fcnt[S.nxt][q], total);
+            base = __shfl_sync(kFull, base, 0);
+            if (lane < nw) s_cnt[q * 32 + lane] = base + incl - c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kTiers; q++) {
+        const unsigned c = Q.n[q];
+        if (c) {
+            int* dst = S.lnxt + S.a->tier_off[q] + s_cnt[q * 32 + wid];
+            for (unsigned i = lane; i < c; i += 32) dst[i] = S.wbuf[woff(q) + i];
+        }
+        Q.n[q] = 0;
+    }
 }
 
 // All 32 lanes call this.  A lane with `fresh` appends v (tier `tier`) to
@@ -181,14 +241,28 @@ __device__ __forceinline__ void warp_push_n(const Sweep& S, WarpQ& Q, uint32_t c
     if (!__any_sync(kFull, cand != 0)) return;
     uint32_t word[N];
     if (S.a->refined) {
-        // refined rule: a candidate read above k is kept only if it is in F_s
+        // refined rule: a candidate read above k is kept if it may still be
+        // evaluating; otherwise its final value decides
+        uint32_t above = 0;
 #pragma unroll
         for (int j = 0; j < N; j++)
-            word[j] = ((cand >> j) & 1u) && (int)(xw[j] & kEstMask) > k
-                          ? __ldcg(S.bmc + (vs[j] >> 5)) : 0xffffffffu;
+            if (((cand >> j) & 1u) && (int)(xw[j] & kEstMask) > k) above |= 1u << j;
+#pragma unroll
+        for (int j = 0; j < N; j++) word[j] = ((above >> j) & 1u) ? __ldcg(S.bmc + (vs[j] >> 5)) : 0u;
+        uint32_t again = 0;
 #pragma unroll
         for (int j = 0; j < N; j++)
-            if (((cand >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) cand &= ~(1u << j);
+            if (((above >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) again |= 1u << j;
+        if (again) {
+            __threadfence();
+#pragma unroll
+            for (int j = 0; j < N; j++) word[j] = ((again >> j) & 1u) ? est_load(S.a->est + vs[j]) : 0u;
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                const int x2 = (int)(word[j] & kEstMask);
+                if (((again >> j) & 1u) && !(h < x2 && x2 <= k)) cand &= ~(1u << j);
+            }
+        }
     }
 #pragma unroll
     for (int j = 0; j < N; j++)
@@ -367,7 +441,10 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
     }
     __syncwarp();
     const bool changed = work && h < k;
-    if (changed) acc.updates += 1;
+    if (changed) {
+        acc.updates += 1;
+        acc.dec += (unsigned long long)(k - h);
+    }
     warp_update(S, changed, u, w, h);
     if (a.sync_mode && a.refined) return;  // activation runs after the update phase
     if (!__any_sync(kFull, changed)) return;
@@ -390,9 +467,23 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
                 word[c] = 0xffffffffu;
             }
         }
+        uint32_t again = 0;
 #pragma unroll
         for (int c = 0; c < kLowCache; c++)
-            if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) cand &= ~(1u << c);
+            if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) again |= 1u << c;
+        if (__any_sync(kFull, again != 0)) {  // refined rule, v done or never in F_s: its final value decides
+            __threadfence();
+#pragma unroll
+            for (int c = 0; c < kLowCache; c++)
+                word[c] = ((again >> c) & 1u) ? est_load(a.est + pv[c]) : 0u;
+#pragma unroll
+            for (int c = 0; c < kLowCache; c++) {
+                const int o = co[c];
+                const int ho = __shfl_sync(kFull, h, o), ko = __shfl_sync(kFull, k, o);
+                const int x2 = (int)(word[c] & kEstMask);
+                if (((again >> c) & 1u) && !(ho < x2 && x2 <= ko)) cand &= ~(1u << c);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < kLowCache; c++)
             word[c] = ((cand >> c) & 1u) ? atomicOr(S.bmn + (pv[c] >> 5), 1u << (pv[c] & 31))
@@ -417,7 +508,7 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
             v = __ldg(a.col + bo + (g - eo));
             xw = est_load(a.est + v);
             const int x = (int)(xw & kEstMask);
-            want = x > ho && (!a.refined || x <= ko || in_current(S, v));
+            want = x > ho && (!a.refined || x <= ko || refined_keep(S, ho, ko, v));
         }
         warp_push(S, Q, want, v, xw >> kEstBits, acc);
     }
@@ -440,7 +531,10 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
         acc.evaluated += 1;
         acc.degsum += (unsigned)d;
     }
-    if (k == 0) return;
+    if (k == 0) {
+        if (S.mark && lane == 0) mark_done(S, u, false);
+        return;
+    }
     int vs[R];
     uint32_t xw[R];
 #pragma unroll
@@ -463,15 +557,123 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
         }
         h = lo;
     }
-    if (h >= k) return;
-    if (lane == 0) acc.updates += 1;
+    if (h >= k) {
+        if (S.mark && lane == 0) mark_done(S, u, false);
+        return;
+    }
+    if (lane == 0) {
+        acc.updates += 1;
+        acc.dec += (unsigned long long)(k - h);
+    }
     warp_update(S, lane == 0, u, w, h);
+    if (S.mark && lane == 0) mark_done(S, u, true);
     if (a.sync_mode && a.refined) return;
     uint32_t cand = 0;
 #pragma unroll
     for (int r = 0; r < R; r++)
         if (vs[r] >= 0 && (int)(xw[r] & kEstMask) > h) cand |= 1u << r;
     warp_push_n<R>(S, Q, cand, h, k, vs, xw, acc);
+}
+
+// Warp tier, degrees above 32 * kMedR (up to kMedBig): one warp per vertex.
+// The first pass gathers the estimates kMedU per lane at a time, keeps
+// y = min(x, k) as 16 bits in the warp's slice of shared memory and counts
+// x >= k; once that count reaches k the estimate stands and the pass stops.
+// Otherwise h < k is found by bisection on t with counts of y >= t taken from
+// shared memory, and a last pass pushes the neighbours with y > h.
+constexpr int kMedU = 8;
+constexpr int kMedSlice = kMedBig / 2;  // words per warp
+
+template <typename Off>
+__device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
+                                               int u, uint32_t* slice, Acc& acc) {
+    const SweepArgs& a = *S.a;
+    const int lane = threadIdx.x & 31;
+    uint16_t* sx = (uint16_t*)slice;
+    const long long b = (long long)rp[u];
+    const int d = (int)((long long)rp[u + 1] - b);
+    const uint32_t w = est_load(a.est + u);
+    const int k = (int)(w & kEstMask);
+    if (lane == 0) {
+        acc.evaluated += 1;
+        acc.degsum += (unsigned)d;
+    }
+    if (k == 0) {
+        if (S.mark && lane == 0) mark_done(S, u, false);
+        return;
+    }
+    const int* colb = a.col + b;
+    int ck = 0, read = d;
+    bool stands = false;
+    for (int j0 = 0; j0 < d; j0 += 32 * kMedU) {
+        int vs[kMedU], xs[kMedU];
+#pragma unroll
+        for (int r = 0; r < kMedU; r++) {
+            const int j = j0 + r * 32 + lane;
+            vs[r] = j < d ? __ldg(colb + j) : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < kMedU; r++) xs[r] = vs[r] >= 0 ? (int)(est_load(a.est + vs[r]) & kEstMask) : -1;
+        int c = 0;
+#pragma unroll
+        for (int r = 0; r < kMedU; r++) {
+            if (xs[r] >= 0) {
+                c += xs[r] >= k ? 1 : 0;
+                sx[j0 + r * 32 + lane] = (uint16_t)(xs[r] < k ? xs[r] : k);
+            }
+        }
+        ck += (int)__reduce_add_sync(kFull, (unsigned)c);
+        if (ck >= k) {
+            stands = true;
+            read = min(d, j0 + 32 * kMedU);
+            break;
+        }
+    }
+    if (lane == 0) acc.skipped += (unsigned long long)(d - read);
+    if (stands) {
+        if (S.mark && lane == 0) mark_done(S, u, false);
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    int lo = 0, hi = k - 1;  // count(y >= 0) = d >= 0 holds; h < k
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        int c = 0;
+        for (int j = lane; j < d; j += 32) c += sx[j] >= mid ? 1 : 0;
+        c = (int)__reduce_add_sync(kFull, (unsigned)c);
+        if (c >= mid) lo = mid;
+        else hi = mid - 1;
+    }
+    const int h = lo;
+    if (lane == 0) {
+        acc.updates += 1;
+        acc.dec += (unsigned long long)(k - h);
+    }
+    warp_update(S, lane == 0, u, w, h);
+    if (S.mark && lane == 0) mark_done(S, u, true);
+    if (a.sync_mode && a.refined) {
+        __syncwarp();
+        return;
+    }
+    for (int j0 = 0; j0 < d; j0 += 32 * kMedU) {
+        int vs[kMedU];
+        uint32_t xw[kMedU];
+        uint32_t cand = 0;
+#pragma unroll
+        for (int r = 0; r < kMedU; r++) {
+            const int j = j0 + r * 32 + lane;
+            const bool want = j < d && (int)sx[j] > h;
+            vs[r] = want ? __ldg(colb + j) : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < kMedU; r++) {
+            xw[r] = vs[r] >= 0 ? est_load(a.est + vs[r]) : 0u;
+            if (vs[r] >= 0 && (int)(xw[r] & kEstMask) > h) cand |= 1u << r;
+        }
+        warp_push_n<kMedU>(S, Q, cand, h, k, vs, xw, acc);
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------- CTA tier
@@ -536,12 +738,79 @@ __device__ __forceinline__ int hub_count_true(const uint32_t* s_hist, int nb, ui
     return r;
 }
 
+// Counts of min(x, k) by power-of-two class, private to each thread: word
+// i * T + tid holds two 16-bit counters, classes 2i and 2i+1.  Conflict-free
+// (a thread's words sit in its own bank) and free of atomics.
+constexpr int kHubP = 4;                    // adjacency loads in flight per thread
+constexpr int kLogClasses = 30;             // estimates are below 2^30
+constexpr int kLogWords = kLogClasses / 2;
+constexpr int kFoldChunks = 65535 / kHubP;  // a 16-bit counter cannot overflow sooner
+
+// Streams colb[0, d) in rounds of T * kHubP entries, kHubP loads in flight
+// per thread.  fn(vs, c) gets this thread's kHubP ids of round c (-1 past d)
+// and returns true to stop (its result must be CTA-uniform).  Returns the
+// entries covered.
+template <class Fn>
+__device__ __forceinline__ long long hub_stream(const int* colb, long long d, Fn fn) {
+    const int T = blockDim.x, tid = threadIdx.x;
+    const long long step = (long long)T * kHubP;
+    const long long nch = (d + step - 1) / step;
+    for (long long c = 0; c < nch; c++) {
+        int vs[kHubP];
+#pragma unroll
+        for (int i = 0; i < kHubP; i++) {
+            const long long j = c * step + (long long)i * T + tid;
+            vs[i] = j < d ? __ldg(colb + j) : -1;
+        }
+        if (fn(vs, c)) return min(d, (c + 1) * step);
+    }
+    return d;
+}
+
+// Histogram of the values y in [lo, hi] in buckets (y - lo) >> shift;
+// y = min(x, k).  nb <= kHubBins.
+__device__ __forceinline__ void hub_hist_pass(const SweepArgs& a, const int* colb, long long d,
+                                              int k, long long lo, long long hi, int shift,
+                                              int nb, uint32_t* s_hist) {
+    const int T = blockDim.x, tid = threadIdx.x;
+    for (int i = tid; i < nb; i += T) s_hist[i] = 0;
+    __syncthreads();
+    hub_stream(colb, d, [&](const int (&vs)[kHubP], long long) {
+        int xs[kHubP];
+#pragma unroll
+        for (int i = 0; i < kHubP; i++) xs[i] = vs[i] >= 0 ? (int)(est_load(a.est + vs[i]) & kEstMask) : -1;
+#pragma unroll
+        for (int i = 0; i < kHubP; i++) {
+            const long long y = xs[i] < k ? xs[i] : k;
+            if (xs[i] >= 0 && y >= lo && y <= hi) atomicAdd(&s_hist[(int)((y - lo) >> shift)], 1u);
+        }
+        return false;
+    });
+    __syncthreads();
+}
+
+// One CTA per hub u with estimate k.
+//   Pass 1 streams the adjacency and counts c_k = #{x >= k}, the no-change
+//   test of the capped h-index: as soon as the CTA's total reaches k the
+//   estimate stands and the pass stops, so a hub whose estimate holds reads
+//   only as much of its adjacency as it takes to find k supporters.
+//   Alongside, each thread counts min(x, k) by power-of-two class.
+//   If c_k < k after the whole adjacency, h < k, and with N_m = #{min(x,k) >=
+//   2^m} the largest m* with N_m* >= 2^m* brackets h in
+//   [2^m*, min(2^(m*+1), k) - 1].  Pass 2 takes the histogram of the values in
+//   the bracket (buckets of one value, or coarse buckets and a further pass
+//   when the bracket is wider than kHubBins) and h is the last t with
+//   #{x >= t} >= t.  A last pass pushes the neighbours.
 template <typename Off>
 __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
-                                           int u, uint32_t* s_hist, uint32_t* wsum, int* s_int,
+                                           int u, uint32_t* s_pool, uint32_t* s_cls,
+                                           uint32_t* s_hub, uint32_t* wsum, int* s_int,
                                            uint32_t* s_u32, Acc& acc) {
     const SweepArgs& a = *S.a;
-    const int T = blockDim.x, tid = threadIdx.x;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = T >> 5;
+    uint32_t* s_lg = s_pool;
+    uint32_t* s_hist = s_pool;
     const long long b = (long long)rp[u];
     const long long d = (long long)rp[u + 1] - b;
     const uint32_t w = est_load(a.est + u);
@@ -550,67 +819,142 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
         acc.evaluated += 1;
         acc.degsum += (unsigned long long)d;
     }
-    if (k == 0) return;
-    // pass 1: histogram of min(x, k) >> shift, with 2^shift the smallest power
-    // of two that brings the k+1 possible values into kHubBins buckets
-    int shift = 0;
-    while ((k >> shift) >= kHubBins) shift++;
-    const long long width = 1LL << shift;
-    const int nb = (k >> shift) + 1;
-    for (int i = tid; i < nb; i += T) s_hist[i] = 0;
-    __syncthreads();
-    for (long long j = tid; j < d; j += T) {
-        const int v = __ldg(a.col + b + j);
-        int x = (int)(est_load(a.est + v) & kEstMask);
-        x = x < k ? x : k;
-        atomicAdd(&s_hist[x >> shift], 1u);
+    if (k == 0) {
+        if (S.mark && tid == 0) mark_done(S, u, false);
+        return;
     }
+    const int* colb = a.col + b;
+#pragma unroll
+    for (int i = 0; i < kLogWords; i++) s_lg[i * T + tid] = 0;
+    if (tid < 32) s_cls[tid] = 0;
+    if (tid == 0) s_hub[0] = 0;
     __syncthreads();
-    const int ntrue = hub_count_true(s_hist, nb, 0u, 0, width, -1, s_u32, wsum, s_int);
-    const int istar = ntrue - 1;
-    int h;
-    if (width == 1) {
-        h = istar;
-    } else {
-        // pass 2: exact counts inside bucket istar; above = #{x >= (istar+1) * width}
-        if (tid == 0) *s_u32 = 0;
-        __syncthreads();
-        hub_count_true(s_hist, nb, 0u, 0, width, istar + 1, s_u32, wsum, s_int);
-        const uint32_t above = *s_u32;
-        __syncthreads();
-        const long long lo = (long long)istar * width;
-        const long long hi = min(lo + width - 1, (long long)k);
-        const int wn = (int)(hi - lo + 1);
-        for (int i = tid; i < wn; i += T) s_hist[i] = 0;
-        __syncthreads();
-        for (long long j = tid; j < d; j += T) {
-            const int v = __ldg(a.col + b + j);
-            int x = (int)(est_load(a.est + v) & kEstMask);
-            x = x < k ? x : k;
-            if (x >= lo && x <= hi) atomicAdd(&s_hist[x - lo], 1u);
+
+    // ---- pass 1
+    const long long step = (long long)T * kHubP;
+    unsigned ck = 0;  // this thread's supporters since the last check
+    bool stands = false;
+    const long long read = hub_stream(colb, d, [&](const int (&vs)[kHubP], long long c) {
+        int xs[kHubP];
+#pragma unroll
+        for (int i = 0; i < kHubP; i++) xs[i] = vs[i] >= 0 ? (int)(est_load(a.est + vs[i]) & kEstMask) : -1;
+#pragma unroll
+        for (int i = 0; i < kHubP; i++) {
+            const int x = xs[i];
+            ck += x >= k ? 1u : 0u;
+            const int y = x < k ? x : k;
+            if (y > 0) {
+                const int m = 31 - __clz(y);
+                s_lg[(m >> 1) * T + tid] += 1u << ((m & 1) << 4);
+            }
         }
+        if ((c + 1) % kFoldChunks == 0) {  // keep the 16-bit counters from overflowing
+#pragma unroll
+            for (int i = 0; i < kLogWords; i++) {
+                const uint32_t v = s_lg[i * T + tid];
+                s_lg[i * T + tid] = 0;
+                if (v & 0xffffu) atomicAdd(&s_cls[2 * i], v & 0xffffu);
+                if (v >> 16) atomicAdd(&s_cls[2 * i + 1], v >> 16);
+            }
+        }
+        const unsigned cs = __reduce_add_sync(kFull, ck);
+        ck = 0;
+        if (lane == 0 && cs) atomicAdd(&s_hub[0], cs);
         __syncthreads();
-        const int nt2 = hub_count_true(s_hist, wn, above, lo, 1, -1, s_u32, wsum, s_int);
-        h = (int)(lo + nt2 - 1);
+        const unsigned tot = s_hub[0];
+        __syncthreads();
+        stands = tot >= (unsigned)k;
+        return stands;
+    });
+    (void)step;
+    if (tid == 0) acc.skipped += (unsigned long long)(d - read);
+    if (stands) {
+        if (S.mark && tid == 0) mark_done(S, u, false);
+        return;
+    }
+    const unsigned c_k = s_hub[0];
+
+    // ---- bracket from the power-of-two classes
+    for (int i = wid; i < kLogWords; i += nw) {
+        unsigned lo = 0, hi = 0;
+        for (int t = lane; t < T; t += 32) {
+            const uint32_t v = s_lg[i * T + t];
+            lo += v & 0xffffu;
+            hi += v >> 16;
+        }
+        lo = __reduce_add_sync(kFull, lo);
+        hi = __reduce_add_sync(kFull, hi);
+        if (lane == 0) {
+            s_cls[2 * i] += lo;
+            s_cls[2 * i + 1] += hi;
+        }
     }
     __syncthreads();
-    if (h >= k) return;
-    if (tid == 0) acc.updates += 1;
-    if ((tid >> 5) == 0) warp_update(S, tid == 0, u, w, h);
+    if (wid == 0) {
+        unsigned c = lane < kLogClasses ? s_cls[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {  // suffix sums: N_m = sum over classes >= m
+            const unsigned t = __shfl_down_sync(kFull, c, o);
+            if (lane + o < 32) c += t;
+        }
+        const bool pred = lane < kLogClasses && (unsigned long long)c >= (1ull << lane);
+        const unsigned bal = __ballot_sync(kFull, pred);
+        const int ms = bal ? 31 - __clz(bal) : -1;
+        const unsigned n_above = __shfl_sync(kFull, c, ms + 1 < 31 ? ms + 1 : 31);
+        if (lane == 0) {
+            s_hub[1] = (uint32_t)ms;
+            s_hub[2] = n_above;
+        }
+    }
+    __syncthreads();
+    const int ms = (int)s_hub[1];
+    int h = 0;
+    if (ms >= 0) {
+        long long lo = 1LL << ms;
+        long long hi = (2 * lo < (long long)k ? 2 * lo : (long long)k) - 1;
+        uint32_t above = 2 * lo <= (long long)k ? s_hub[2] : c_k;  // #{x >= hi + 1}
+        for (;;) {
+            int shift = 0;
+            while (((hi - lo) >> shift) >= kHubBins) shift++;
+            const int nb = (int)((hi - lo) >> shift) + 1;
+            hub_hist_pass(a, colb, d, k, lo, hi, shift, nb, s_hist);
+            const int nt = hub_count_true(s_hist, nb, above, lo, 1LL << shift, -1, s_u32, wsum, s_int);
+            if (shift == 0) {
+                h = (int)(lo + nt - 1);
+                break;
+            }
+            const int istar = nt - 1;
+            if (tid == 0) *s_u32 = 0;
+            __syncthreads();
+            hub_count_true(s_hist, nb, above, lo, 1LL << shift, istar + 1, s_u32, wsum, s_int);
+            above = *s_u32;
+            __syncthreads();
+            lo += (long long)istar << shift;
+            hi = min(lo + (1LL << shift) - 1, hi);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        acc.updates += 1;
+        acc.dec += (unsigned long long)(k - h);
+    }
+    if (wid == 0) warp_update(S, tid == 0, u, w, h);
+    if (S.mark && tid == 0) mark_done(S, u, true);
     if (a.sync_mode && a.refined) return;
-    for (long long j0 = 0; j0 < d; j0 += T) {
-        const long long j = j0 + tid;
-        bool want = false;
-        int v = 0;
-        uint32_t tier = 0;
-        if (j < d) {
-            v = __ldg(a.col + b + j);
-            const uint32_t xw = est_load(a.est + v);
-            want = should_push(S, h, k, (int)(xw & kEstMask), v);
-            tier = xw >> kEstBits;
-        }
-        if (__any_sync(kFull, want)) warp_push(S, Q, want, v, tier, acc);
-    }
+
+    // ---- activation
+    hub_stream(colb, d, [&](const int (&vs)[kHubP], long long) {
+        uint32_t xw[kHubP];
+        uint32_t cand = 0;
+#pragma unroll
+        for (int i = 0; i < kHubP; i++) xw[i] = vs[i] >= 0 ? est_load(a.est + vs[i]) : 0u;
+#pragma unroll
+        for (int i = 0; i < kHubP; i++)
+            if (vs[i] >= 0 && (int)(xw[i] & kEstMask) > h) cand |= 1u << i;
+        warp_push_n<kHubP>(S, Q, cand, h, k, vs, xw, acc);
+        return false;
+    });
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- barriers
@@ -648,14 +992,21 @@ __device__ __forceinline__ void block_barrier() { __syncthreads(); }
 // ---------------------------------------------------------------- kernel
 template <typename Off, int T>
 __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs a) {
-    __shared__ uint32_t s_hist[kHubBins];
-    __shared__ uint32_t s_lowh[kMaxBlock / 32][(T / 4) * 32];
+    // Dynamic shared memory: the warps' push buffers, then one pool that
+    // serves, one after the other within a sweep, the CTA tier (power-of-two
+    // counters, then the bracket histogram), the warp tier's staged estimates
+    // and the thread tier's per-warp counts (sizes: sweep_smem_bytes).
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    int* s_wbuf = (int*)s_dyn;
+    uint32_t* s_pool = s_dyn + (blockDim.x >> 5) * kWCap;
+    __shared__ uint32_t s_cls[32];
+    __shared__ uint32_t s_cnt[3 * 32];
+    __shared__ uint32_t s_hub[4];
     __shared__ uint32_t s_wsum[32];
     __shared__ unsigned long long s_acc[kAccN];
     __shared__ long long s_b[12];
     __shared__ int s_int[2];
     __shared__ uint32_t s_u32;
-    __shared__ int s_wbuf[kMaxBlock / 32][kWCap];
 
     const Off* rp = (const Off*)a.row_ptr;
     SweepCtl* ctl = a.ctl;
@@ -666,7 +1017,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
     bool prev_tail = tail;
     unsigned my_epoch = 0;
     unsigned nbar = 0;
-    unsigned long long tot[kAccN] = {0, 0, 0, 0};  // block 0, thread 0: run totals
+    unsigned long long tot[kAccN] = {0, 0, 0, 0, 0, 0};  // block 0, thread 0: run totals
     long long tail_sweeps = 0;
     long long s = a.first_sweep;
     if (tid == 0) {
@@ -686,7 +1037,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
             const unsigned f2 = __ldcg(&ctl->fcnt[cur][2]);
             const int st = __ldcg(&ctl->status);
             unsigned pv[kTiers] = {0u, 0u, 0u};
-            unsigned long long av[kAccN] = {0, 0, 0, 0};
+            unsigned long long av[kAccN] = {0, 0, 0, 0, 0, 0};
             if (s > 0)
                 for (int q = 0; q < kTiers; q++) pv[q] = __ldcg(&ctl->fcnt[prv][q]);
             const bool book = blockIdx.x == 0 && s > a.first_sweep;
@@ -703,14 +1054,17 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                     ctl->acc[prv][i] = 0;
                 }
                 if (s - 1 < a.max_trace) {
-                    a.trace[(s - 1) * 4 + 0] = (long long)av[kAccEvaluated];
-                    a.trace[(s - 1) * 4 + 1] = (long long)av[kAccDegsum];
-                    a.trace[(s - 1) * 4 + 2] = (long long)av[kAccUpdates];
+                    long long* tr = a.trace + (s - 1) * kTraceCols;
+                    tr[kTrFrontier] = (long long)av[kAccEvaluated];
+                    tr[kTrDegsum] = (long long)av[kAccDegsum];
+                    tr[kTrUpdates] = (long long)av[kAccUpdates];
+                    tr[kTrRead] = (long long)(av[kAccDegsum] - av[kAccSkipped]);
+                    tr[kTrDec] = (long long)av[kAccDec];
                 }
                 if (prev_tail) tail_sweeps += 1;
             }
             // start time of sweep s (globaltimer, ns)
-            if (blockIdx.x == 0 && s < a.max_trace) a.trace[s * 4 + 3] = (long long)gtime_ns();
+            if (blockIdx.x == 0 && s < a.max_trace) a.trace[s * kTraceCols + kTrStart] = (long long)gtime_ns();
             // slot of sweep s-2: free now, push target of sweep s+1
             if (blockIdx.x == 0) {
                 const int old = (int)((s + 2) % kSlots);
@@ -798,10 +1152,12 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
         S.lcur = (s == 0 && a.init_list) ? a.init_list : a.list[p_cur];
         S.lnxt = a.list[p_nxt];
         S.bmc = a.bitmap[p_cur];
+        S.bmc_w = a.bitmap[p_cur];
+        S.mark = a.refined && !a.sync_mode;
         S.bmn = a.bitmap[p_nxt];
-        S.wbuf = s_wbuf[wid];
+        S.wbuf = s_wbuf + wid * kWCap;
         WarpQ Q = {{0u, 0u, 0u}};
-        Acc acc = {0, 0, 0, 0};
+        Acc acc = {0u, 0u, 0u, 0ull, 0ull, 0ull};
         const unsigned warps_all = (tail ? 1u : gridDim.x) * (unsigned)nwarps;
         const long long gthreads = tail ? blockDim.x : (long long)gridDim.x * blockDim.x;
         const long long gt = tail ? tid : (long long)blockIdx.x * blockDim.x + tid;
@@ -833,7 +1189,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                 __syncthreads();
                 if (i >= c2) break;
                 const int u = list_load(S.lcur + a.tier_off[2] + i);
-                hub_vertex<Off>(S, Q, rp, u, s_hist, s_wsum, &s_int[0], &s_u32, acc);
+                hub_vertex<Off>(S, Q, rp, u, s_pool, s_cls, s_hub, s_wsum, &s_int[0], &s_u32, acc);
                 __syncthreads();
             }
         }
@@ -844,7 +1200,9 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
             run_tier(&ctl->cursor[cur][1], c1, wi, [&](unsigned i0, unsigned i1) {
                 for (unsigned i = i0; i < i1; i++) {
                     const int u = list_load(S.lcur + a.tier_off[1] + i);
-                    med_vertex<Off, kMedR>(S, Q, rp, u, acc);
+                    const long long du = (long long)rp[u + 1] - (long long)rp[u];
+                    if (du <= 32 * kMedR) med_vertex<Off, kMedR>(S, Q, rp, u, acc);
+                    else med_big_vertex<Off>(S, Q, rp, u, s_pool + wid * kMedSlice, acc);
                 }
             });
         }
@@ -860,7 +1218,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                     for (unsigned base = i0; base < i1; base += 32u) {
                         const unsigned i = base + (unsigned)lane;
                         low_warp<Off, T / 4, true>(S, Q, rp, i < i1, (int)i, S.bmc + (base >> 5),
-                                                   s_lowh[wid], acc);
+                                                   s_pool + wid * kMedSlice, acc);
                     }
                 });
             } else {
@@ -869,7 +1227,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                         const unsigned i = base + (unsigned)lane;
                         const bool valid = i < i1;
                         const int u = valid ? list_load(S.lcur + a.tier_off[0] + i) : 0;
-                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, nullptr, s_lowh[wid], acc);
+                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, nullptr, s_pool + wid * kMedSlice, acc);
                     }
                 });
             }
@@ -914,11 +1272,12 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                 }
             }
         }
-        warp_flush_all(S, Q);
+        cta_flush_all(S, Q, s_cnt);
 
         // ---- per-sweep statistics
         {
-            unsigned long long v4[kAccN] = {acc.evaluated, acc.degsum, acc.updates, acc.pushes};
+            unsigned long long v4[kAccN] = {acc.evaluated, acc.degsum, acc.updates,
+                                            acc.pushes,    acc.skipped, acc.dec};
 #pragma unroll
             for (int i = 0; i < kAccN; i++) {
                 unsigned long long x = v4[i];
@@ -958,6 +1317,23 @@ const void* pick_kernel(int t_lo, int off64) {
     return off64 ? (const void*)k_sweep<long long, 16> : (const void*)k_sweep<int, 16>;
 }
 
+// Dynamic shared memory of one CTA: push buffers, then the pool (the largest
+// of the CTA tier's counters, its histogram and every warp's kMedBig 16-bit
+// estimates).
+size_t sweep_smem_bytes(int block) {
+    const size_t nw = (size_t)block / 32;
+    const size_t pool = std::max<size_t>({(size_t)kLogWords * block, (size_t)kHubBins, nw * kMedSlice});
+    static_assert((16 / 4) * 32 <= kMedSlice, "thread tier counts exceed a warp's slice");
+    return sizeof(uint32_t) * (nw * kWCap + pool);
+}
+
+cudaError_t prepare(const void* fn, int block, int* per_sm) {
+    const size_t smem = sweep_smem_bytes(block);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, block, smem);
+}
+
 }  // namespace
 
 cudaError_t sweep_max_grid(int block, int t_lo, int t_hi, int off64, int* grid) {
@@ -967,7 +1343,7 @@ cudaError_t sweep_max_grid(int block, int t_lo, int t_hi, int off64, int* grid) 
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(t_lo, off64), block, 0);
+    e = prepare(pick_kernel(t_lo, off64), block, &per_sm);
     if (e != cudaSuccess) return e;
     *grid = sms * per_sm;
     return cudaSuccess;
@@ -981,7 +1357,7 @@ cudaError_t launch_sweep(const SweepArgs& a, int block, int grid_req, int ctas_p
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const void* fn = pick_kernel(a.t_lo, a.off64);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
+    e = prepare(fn, block, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
@@ -991,7 +1367,7 @@ cudaError_t launch_sweep(const SweepArgs& a, int block, int grid_req, int ctas_p
     *grid_used = grid;
     void* args[] = {(void*)&a};
     count_launch();
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, sweep_smem_bytes(block), st);
 }
 
 cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cudaStream_t st) {

@@ -44,7 +44,7 @@ def test_python_binding_covers_every_symbol():
 def test_defaults_and_version():
     o = K.default_options()
     assert o.struct_size == ctypes.sizeof(K.Options)
-    assert (o.t_lo, o.t_hi, o.block) == (16, 256, 512)
+    assert (o.t_lo, o.t_hi, o.block) == (16, 2048, 512)
     assert o.timeout_s > 0
     assert "sm_103a" in K.version()
     s = K.default_serve_options()

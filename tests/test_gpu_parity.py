@@ -94,20 +94,24 @@ def test_random_graphs_match_oracle(torch_cuda, seed):
         np.testing.assert_array_equal(gcol, col)
         np.testing.assert_array_equal(g.run().cpu().numpy(), core)
         np.testing.assert_array_equal(g.run(device=False), core)
+        np.testing.assert_array_equal(g.run(refined=True).cpu().numpy(), core)
 
 
+@pytest.mark.parametrize("refined", [False, True])
 @pytest.mark.parametrize("opts", [
     dict(t_lo=1, t_hi=1),                  # everything above degree 1 in the CTA tier
     dict(t_lo=2, t_hi=32),
     dict(t_lo=8, t_hi=64, block=64),
     dict(t_lo=16, t_hi=256, block=256),
+    dict(t_lo=16, t_hi=2048),              # staged warp tier up to degree 2048
+    dict(t_lo=4, t_hi=1024, block=128),
     dict(tail_max=-1),                     # no single-CTA tail
     dict(tail_max=1 << 30),                # single CTA from the start
     dict(max_ctas=1),
     dict(max_ctas=3, low_chunk=1, med_chunk=1),
     dict(low_chunk=8, med_chunk=64),
 ])
-def test_launch_shapes_and_tiers_match_oracle(torch_cuda, opts):
+def test_launch_shapes_and_tiers_match_oracle(torch_cuda, opts, refined):
     rng = np.random.default_rng(7)
     n = 20000
     src, dst = random_graph(rng, n, 6 * n, hubs=5, hub_deg=2000)
@@ -115,25 +119,47 @@ def test_launch_shapes_and_tiers_match_oracle(torch_cuda, opts):
     src = np.concatenate([src, g2.src])
     dst = np.concatenate([dst, g2.dst])
     _, _, core = oracle_of(n, src, dst)
-    got, st = gpu_coreness(n, src, dst, options=K.default_options(**opts))
+    got, st = gpu_coreness(n, src, dst, options=K.default_options(**opts), refined=refined)
     np.testing.assert_array_equal(got, core)
     assert st["status"] == 0 and st["sweeps"] >= 1
 
 
-def test_hub_two_pass_histogram(torch_cuda):
-    """A dense block whose estimates exceed the 4096-bucket hub histogram, so the
-    coarse-then-fine bucket path runs."""
+@pytest.mark.parametrize("refined", [False, True])
+def test_hub_bracket_wider_than_histogram(torch_cuda, refined):
+    """A dense block whose coreness exceeds 8192: the power-of-two bracket
+    [8192, 16383] is wider than the 4096-bucket hub histogram, so the coarse
+    buckets and the fine pass both run."""
     rng = np.random.default_rng(1)
-    k = 4600
+    k = 8600
     a, b = np.triu_indices(k, 1)
-    keep = rng.random(a.shape[0]) < 0.97
+    keep = rng.random(a.shape[0]) < 0.99
     n = k + 3000
     src = np.concatenate([a[keep], rng.integers(0, n, 20000)]).astype(np.int32)
     dst = np.concatenate([b[keep], rng.integers(0, n, 20000)]).astype(np.int32)
     _, _, core = oracle_of(n, src, dst)
-    assert core.max() >= 4096
-    got, _ = gpu_coreness(n, src, dst)
+    assert core.max() >= 8192
+    got, _ = gpu_coreness(n, src, dst, refined=refined)
     np.testing.assert_array_equal(got, core)
+
+
+def test_hub_early_exit_and_entries_read(torch_cuda):
+    """Hubs whose estimate holds stop reading once they found k supporters:
+    entries_read stays below the frontier degree sum, and the result is exact."""
+    rng = np.random.default_rng(4)
+    k = 600
+    a, b = np.triu_indices(k, 1)
+    n = 2_000_000
+    hubs = np.arange(k, dtype=np.int32)
+    # each clique member also gets many low-degree leaves after its clique edges
+    leaf_src = np.repeat(hubs, 20000)
+    leaf_dst = rng.integers(k, n, leaf_src.shape[0]).astype(np.int32)
+    src = np.concatenate([a, leaf_src]).astype(np.int32)
+    dst = np.concatenate([b, leaf_dst]).astype(np.int32)
+    _, _, core = oracle_of(n, src, dst)
+    got, st = gpu_coreness(n, src, dst)
+    np.testing.assert_array_equal(got, core)
+    assert st["entries_read"] < st["edges_scanned"]
+    assert st["decrease"] > 0
 
 
 def test_csr_input_paths(torch_cuda):
@@ -179,7 +205,7 @@ def test_invalid_inputs_are_rejected(torch_cuda):
                          options=K.default_options(t_lo=64))
     with pytest.raises(K.KCoreError):
         K.Graph.from_coo(3, np.array([0], np.int32), np.array([1], np.int32),
-                         options=K.default_options(t_hi=512))
+                         options=K.default_options(t_hi=4096))
 
 
 def test_repeated_runs_identical(torch_cuda):
@@ -246,3 +272,7 @@ def test_workload_full_size_matches_oracle(torch_cuda, name):
         st = g.stats()
         assert st["status"] == 0
         assert st["evaluated"] >= g0.n
+        deg = np.diff(grp.astype(np.int64))
+        assert st["decrease"] == int(deg.sum()) - int(core.astype(np.int64).sum())
+        np.testing.assert_array_equal(g.run(refined=True).cpu().numpy(), core)
+        assert g.stats()["decrease"] == st["decrease"]

@@ -11,11 +11,17 @@ relies on (readings H4/H5):
 * the refined rule of Sec. IV with the extra clause "or v is in the current
   frontier" always ends at the coreness;
 * the refined rule alone (push v iff new_u < x <= old_u) does not: some
-  schedule leaves an estimate above the coreness.
+  schedule leaves an estimate above the coreness;
+* the narrowed clause the kernel uses also always ends at the coreness: a
+  vertex marks itself done once evaluated, and for a done vertex (or one not
+  in the frontier) the refined test is applied to a value of est[v] read
+  after seeing the mark (v's final value of the sweep);
+* applying the refined test to the value read before the mark is unsafe.
 """
 import random
 
 import numpy as np
+import pytest
 
 import oracle
 from tests import refimpl
@@ -36,6 +42,7 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000):
         order = list(frontier)
         rng.shuffle(order)
         nxt = set()
+        done = set()
 
         def read(v):                          # stale or fresh, at random
             return start[v] if rng.random() < 0.5 else est[v]
@@ -43,6 +50,7 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000):
         for u in order:
             k = est[u]
             h = capped_hindex([read(v) for v in adj[u]], k)
+            done.add(u)
             if h >= k:
                 continue
             est[u] = h
@@ -52,6 +60,16 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000):
                     push = h < x
                 elif rule == "refined_frontier":
                     push = h < x and (x <= k or v in frontier)
+                elif rule == "refined_done":
+                    if h < x and x > k and v in frontier and v not in done:
+                        push = True           # v may still be reading u's old value
+                    elif h < x and x > k:
+                        x2 = est[v]           # read again after seeing v done
+                        push = h < x2 <= k
+                    else:
+                        push = h < x
+                elif rule == "refined_done_stale":
+                    push = h < x and (x <= k or (v in frontier and v not in done))
                 else:                         # refined alone
                     push = h < x and x <= k
                 if push:
@@ -83,12 +101,13 @@ def test_safe_rules_always_reach_the_coreness():
         n = rng.randint(2, 24)
         adj = random_graph(rng, n, rng.uniform(0.1, 0.6))
         core = coreness(n, adj)
-        for rule in ("simple", "refined_frontier"):
+        for rule in ("simple", "refined_frontier", "refined_done"):
             for _ in range(3):
                 assert run_async(n, adj, rule, rng) == core, (trial, rule)
 
 
-def test_refined_rule_alone_can_fail_in_place():
+@pytest.mark.parametrize("rule", ["refined_alone", "refined_done_stale"])
+def test_unsafe_refined_variants_can_fail_in_place(rule):
     rng = random.Random(7)
     failures = 0
     for trial in range(400):
@@ -96,7 +115,7 @@ def test_refined_rule_alone_can_fail_in_place():
         adj = random_graph(rng, n, rng.uniform(0.2, 0.6))
         core = coreness(n, adj)
         for _ in range(4):
-            est = run_async(n, adj, "refined_alone", rng)
+            est = run_async(n, adj, rule, rng)
             assert all(e >= c for e, c in zip(est, core))   # never below the coreness
             failures += est != core
     assert failures > 0
