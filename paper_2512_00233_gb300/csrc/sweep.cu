@@ -14,9 +14,9 @@
 //   refined (Sec. IV, Further Optimizations):         push v iff h < x and
 //           (x <= k  or  v may still be evaluating in this sweep).
 // Only v writes est[v], and only while it is evaluated.  A vertex of F_s
-// clears its own membership bit once its evaluation is over (after a fence
-// that orders its estimate store first).  When u finds v's bit clear (v is
-// done, or was never in F_s), it reads est[v] again, after a fence, and
+// clears its own membership bit once its evaluation is over (a release, after
+// its estimate store).  When u finds v's bit clear with an acquire read (v is
+// done, or was never in F_s), it reads est[v] again and
 // applies FastK's condition h < x <= k to that value: v's final value of the
 // sweep.  If it exceeds k, v's h-index never counted u (u's value was at most
 // k), so u's decrease cannot lower it.  When v's bit is still set, v may be
@@ -72,9 +72,6 @@ __device__ __forceinline__ unsigned long long gtime_ns() {
 __device__ __forceinline__ unsigned vload(const unsigned* p) { return *(const volatile unsigned*)p; }
 __device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
 __device__ __forceinline__ long long vload(const long long* p) { return *(const volatile long long*)p; }
-__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
-    return *(const volatile unsigned long long*)p;
-}
 
 // Estimates, lists and bitmaps are read through L2 (ld.global.cg): another SM
 // may have written them, and an L1 copy from an earlier sweep would be stale.
@@ -116,25 +113,30 @@ struct WarpQ {
     unsigned n[kTiers];
 };
 
-__device__ __forceinline__ bool in_current(const Sweep& S, int v) {
-    return (__ldcg(S.bmc + (v >> 5)) >> (v & 31)) & 1u;
+// Membership word read with acquire semantics: once v's bit is seen clear,
+// v's estimate store made before its release is visible.
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Refined rule for a neighbour v read as x > k while u goes from k to h:
-// keep v if it may still be evaluating (bit set); otherwise decide on its
-// final value, read after the bit.
-__device__ __forceinline__ bool refined_keep(const Sweep& S, int h, int k, int v) {
-    if (in_current(S, v)) return true;
-    __threadfence();
+// Refined rule (asynchronous) for a neighbour v read as x, h < x, while u
+// goes from k to h: push if x <= k or v may still be evaluating (bit set);
+// otherwise decide on v's final value, read after the bit.
+__device__ __forceinline__ bool refined_push(const Sweep& S, int h, int k, int v, int x) {
+    if (x <= k) return true;
+    if ((ld_acquire(S.bmc + (v >> 5)) >> (v & 31)) & 1u) return true;
     const int x2 = (int)(est_load(S.a->est + v) & kEstMask);
     return h < x2 && x2 <= k;
 }
 
 // Marks u's evaluation in sweep s as over (warp and CTA tiers, refined
-// asynchronous mode): after its estimate store, clears its F_s bit.
-__device__ __forceinline__ void mark_done(const Sweep& S, int u, bool wrote) {
-    if (wrote) __threadfence();
-    atomicAnd(S.bmc_w + (u >> 5), ~(1u << (u & 31)));
+// asynchronous mode): clears its F_s bit with release semantics, after its
+// estimate store.
+__device__ __forceinline__ void mark_done(const Sweep& S, int u) {
+    const uint32_t m = ~(1u << (u & 31));
+    asm volatile("red.release.gpu.global.and.b32 [%0], %1;" ::"l"(S.bmc_w + (u >> 5)), "r"(m) : "memory");
 }
 
 // Appends the warp's buffered pushes of tier q to the global list.  All 32
@@ -150,11 +152,6 @@ __device__ __forceinline__ void warp_flush(const Sweep& S, WarpQ& Q, int q) {
     for (unsigned i = lane; i < c; i += 32) dst[i] = S.wbuf[woff(q) + i];
     __syncwarp();
     Q.n[q] = 0;
-}
-
-__device__ __forceinline__ void warp_flush_all(const Sweep& S, WarpQ& Q) {
-#pragma unroll
-    for (int q = 0; q < kTiers; q++) warp_flush(S, Q, q);
 }
 
 // End-of-sweep flush of every warp's push buffers with one global atomic per
@@ -243,18 +240,17 @@ __device__ __forceinline__ void warp_push_n(const Sweep& S, WarpQ& Q, uint32_t c
     if (S.a->refined) {
         // refined rule: a candidate read above k is kept if it may still be
         // evaluating; otherwise its final value decides
-        uint32_t above = 0;
+        uint32_t chk = 0;
 #pragma unroll
         for (int j = 0; j < N; j++)
-            if (((cand >> j) & 1u) && (int)(xw[j] & kEstMask) > k) above |= 1u << j;
+            if (((cand >> j) & 1u) && (int)(xw[j] & kEstMask) > k) chk |= 1u << j;
 #pragma unroll
-        for (int j = 0; j < N; j++) word[j] = ((above >> j) & 1u) ? __ldcg(S.bmc + (vs[j] >> 5)) : 0u;
+        for (int j = 0; j < N; j++) word[j] = ((chk >> j) & 1u) ? ld_acquire(S.bmc + (vs[j] >> 5)) : 0u;
         uint32_t again = 0;
 #pragma unroll
         for (int j = 0; j < N; j++)
-            if (((above >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) again |= 1u << j;
+            if (((chk >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) again |= 1u << j;
         if (again) {
-            __threadfence();
 #pragma unroll
             for (int j = 0; j < N; j++) word[j] = ((again >> j) & 1u) ? est_load(S.a->est + vs[j]) : 0u;
 #pragma unroll
@@ -462,7 +458,7 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
             pv[c] = cv[c];
             if (cv[c] >= 0 && ch && x > ho) {
                 cand |= 1u << c;
-                word[c] = (a.refined && x > ko) ? __ldcg(S.bmc + (cv[c] >> 5)) : 0xffffffffu;
+                word[c] = (a.refined && x > ko) ? ld_acquire(S.bmc + (cv[c] >> 5)) : 0xffffffffu;
             } else {
                 word[c] = 0xffffffffu;
             }
@@ -472,7 +468,6 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
         for (int c = 0; c < kLowCache; c++)
             if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) again |= 1u << c;
         if (__any_sync(kFull, again != 0)) {  // refined rule, v done or never in F_s: its final value decides
-            __threadfence();
 #pragma unroll
             for (int c = 0; c < kLowCache; c++)
                 word[c] = ((again >> c) & 1u) ? est_load(a.est + pv[c]) : 0u;
@@ -508,7 +503,7 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
             v = __ldg(a.col + bo + (g - eo));
             xw = est_load(a.est + v);
             const int x = (int)(xw & kEstMask);
-            want = x > ho && (!a.refined || x <= ko || refined_keep(S, ho, ko, v));
+            want = x > ho && (!a.refined || refined_push(S, ho, ko, v, x));
         }
         warp_push(S, Q, want, v, xw >> kEstBits, acc);
     }
@@ -532,7 +527,7 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
         acc.degsum += (unsigned)d;
     }
     if (k == 0) {
-        if (S.mark && lane == 0) mark_done(S, u, false);
+        if (S.mark && lane == 0) mark_done(S, u);
         return;
     }
     int vs[R];
@@ -558,7 +553,7 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
         h = lo;
     }
     if (h >= k) {
-        if (S.mark && lane == 0) mark_done(S, u, false);
+        if (S.mark && lane == 0) mark_done(S, u);
         return;
     }
     if (lane == 0) {
@@ -566,7 +561,7 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
         acc.dec += (unsigned long long)(k - h);
     }
     warp_update(S, lane == 0, u, w, h);
-    if (S.mark && lane == 0) mark_done(S, u, true);
+    if (S.mark && lane == 0) mark_done(S, u);
     if (a.sync_mode && a.refined) return;
     uint32_t cand = 0;
 #pragma unroll
@@ -599,7 +594,7 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
         acc.degsum += (unsigned)d;
     }
     if (k == 0) {
-        if (S.mark && lane == 0) mark_done(S, u, false);
+        if (S.mark && lane == 0) mark_done(S, u);
         return;
     }
     const int* colb = a.col + b;
@@ -631,7 +626,7 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
     }
     if (lane == 0) acc.skipped += (unsigned long long)(d - read);
     if (stands) {
-        if (S.mark && lane == 0) mark_done(S, u, false);
+        if (S.mark && lane == 0) mark_done(S, u);
         __syncwarp();
         return;
     }
@@ -651,7 +646,7 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
         acc.dec += (unsigned long long)(k - h);
     }
     warp_update(S, lane == 0, u, w, h);
-    if (S.mark && lane == 0) mark_done(S, u, true);
+    if (S.mark && lane == 0) mark_done(S, u);
     if (a.sync_mode && a.refined) {
         __syncwarp();
         return;
@@ -820,7 +815,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
         acc.degsum += (unsigned long long)d;
     }
     if (k == 0) {
-        if (S.mark && tid == 0) mark_done(S, u, false);
+        if (S.mark && tid == 0) mark_done(S, u);
         return;
     }
     const int* colb = a.col + b;
@@ -869,7 +864,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
     (void)step;
     if (tid == 0) acc.skipped += (unsigned long long)(d - read);
     if (stands) {
-        if (S.mark && tid == 0) mark_done(S, u, false);
+        if (S.mark && tid == 0) mark_done(S, u);
         return;
     }
     const unsigned c_k = s_hub[0];
@@ -939,7 +934,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
         acc.dec += (unsigned long long)(k - h);
     }
     if (wid == 0) warp_update(S, tid == 0, u, w, h);
-    if (S.mark && tid == 0) mark_done(S, u, true);
+    if (S.mark && tid == 0) mark_done(S, u);
     if (a.sync_mode && a.refined) return;
 
     // ---- activation
@@ -1213,12 +1208,12 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
             const bool dense = (long long)c0 * 2 >= a.n;
             const unsigned items = dense ? (unsigned)a.n : c0;
             const unsigned wi = 32u * max(1u, min((unsigned)a.low_chunk, items / (32u * warps_all)));
+            uint32_t* hist = s_pool + wid * kMedSlice;
             if (dense) {
                 run_tier(&ctl->cursor[cur][3], items, wi, [&](unsigned i0, unsigned i1) {
                     for (unsigned base = i0; base < i1; base += 32u) {
                         const unsigned i = base + (unsigned)lane;
-                        low_warp<Off, T / 4, true>(S, Q, rp, i < i1, (int)i, S.bmc + (base >> 5),
-                                                   s_pool + wid * kMedSlice, acc);
+                        low_warp<Off, T / 4, true>(S, Q, rp, i < i1, (int)i, S.bmc + (base >> 5), hist, acc);
                     }
                 });
             } else {
@@ -1227,7 +1222,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                         const unsigned i = base + (unsigned)lane;
                         const bool valid = i < i1;
                         const int u = valid ? list_load(S.lcur + a.tier_off[0] + i) : 0;
-                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, nullptr, s_pool + wid * kMedSlice, acc);
+                        low_warp<Off, T / 4, false>(S, Q, rp, valid, u, nullptr, hist, acc);
                     }
                 });
             }
