@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--stream-count", type=int, default=1000)
     ap.add_argument("--arena-gib", type=int, default=8)
     ap.add_argument("--chunk-sweeps", type=int, default=16)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the sweep knobs on the workload first (paper_2512_00233_gb300.autotune)")
+    ap.add_argument("--graph", action="store_true",
+                    help="decomposition-only runs replay a captured CUDA graph (KCORE_GRAPH)")
     return ap.parse_args()
 
 
@@ -312,8 +316,16 @@ def run_ours(args):
     def flush_l2():
         flush.add_(1)
 
+    opts = None
+    tuned = None
+    if args.autotune:
+        from paper_2512_00233_gb300 import autotune
+        with K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes) as gt:
+            opts, _ = autotune.autotune(gt, reps=2, passes=1, cache=None)
+        tuned = {k: getattr(opts, k) for k in autotune.SPACE}
+
     def step_device():
-        g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes)
+        g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes, options=opts)
         g.run(out=out_d)
         return g
 
@@ -348,17 +360,17 @@ def run_ours(args):
     local_ms, value = combine_ranks(sum(step_ms), m, args.steps, device=dev)
 
     # ---- decomposition alone on the resident graph (paper's timing)
-    g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes)
+    g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes, options=opts)
     run_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
     sweep_stats = []
     for _ in range(2):
         flush_l2()
-        g.run(out=out_d)
+        g.run(out=out_d, graph=args.graph)
     for i in range(args.steps):
         flush_l2()
         run_ev[i][0].record(stream)
-        g.run(out=out_d)
+        g.run(out=out_d, graph=args.graph)
         run_ev[i][1].record(stream)
         sweep_stats.append(g.stats())
     torch.cuda.synchronize()
@@ -374,7 +386,7 @@ def run_ours(args):
         flush_l2()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        gh = K.Graph.from_coo(g0.n, src_h.numpy(), dst_h.numpy(), rp_bytes)
+        gh = K.Graph.from_coo(g0.n, src_h.numpy(), dst_h.numpy(), rp_bytes, options=opts)
         gh.run(out=out_h.numpy())
         t1 = time.perf_counter()
         gh.close()
@@ -399,7 +411,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": g0.name, "n": g0.n, "samples": g0.samples, "m": m,
                        "row_ptr_bytes": rp_bytes, "l2": "512 MiB buffer rewritten between steps",
-                       "step": "kcore_create_coo (device samples) + kcore_run (device output)"},
+                       "step": "kcore_create_coo (device samples) + kcore_run (device output)",
+                       "options": tuned or "library defaults"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * g0.samples,
                     "d2h_bytes_per_step": 4 * g0.n},
             "gpu_launches": launches,
@@ -410,7 +423,8 @@ def run_ours(args):
                           "tail_sweeps": statistics.mean(s["tail_sweeps"] for s in sweep_stats),
                           "evaluated": statistics.mean(s["evaluated"] for s in sweep_stats),
                           "edges_scanned": statistics.mean(s["edges_scanned"] for s in sweep_stats),
-                          "grid": sweep_stats[0]["grid"], "block": sweep_stats[0]["block"]},
+                          "grid": sweep_stats[0]["grid"], "block": sweep_stats[0]["block"],
+                          "cuda_graph": bool(args.graph)},
             "roofline": {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -260,7 +260,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(torch_cuda):
 
 
 # ------------------------------------------------------------------ named workloads
-@pytest.mark.parametrize("name", ["er10k", "road2048", "rmat22"])
+@pytest.mark.parametrize("name", ["er10k", "road2048", "rmat22", "rmat24_planted"])
 def test_workload_full_size_matches_oracle(torch_cuda, name):
     g0 = graphgen.workload(name)
     rp, col, core = oracle_of(g0.n, g0.src, g0.dst)
