@@ -190,7 +190,9 @@ kcore_status kcore_copy_csr(const kcore_graph* g, void* row_ptr_out, int32_t* co
  * 2 row_ptr entries + est[u], then one col_idx entry and one estimate gather
  * per adjacency entry read (entries_read: deg(u), or fewer when the
  * no-change test of a high-degree vertex found est[u] supporters early),
- * plus 4 bytes per update.
+ * plus 4 bytes per update, plus the initialisation and output of the run
+ * (estimates from the degrees, three frontier bitmaps, coreness written out:
+ * 16 bytes per vertex and 12 bytes per 32 vertices).
  */
 typedef struct kcore_run_stats {
     int64_t n, nnz;             /* graph size (nnz = 2m)                              */

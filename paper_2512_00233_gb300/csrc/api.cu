@@ -11,8 +11,6 @@
 #include "kc_common.cuh"
 
 namespace kc {
-cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cudaStream_t st);
-cudaError_t launch_output(const uint32_t* est, int* out, long long n, cudaStream_t st);
 
 static thread_local std::string t_err;
 static std::atomic<long long> g_launches{0};
@@ -432,13 +430,10 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
     const int64_t n = g->csr.n;
     const bool sync_mode = (flags & KCORE_SYNC_MODE) != 0;
     const size_t words = (size_t)((n + 31) / 32);
+    // The launch itself initialises the estimates and the frontier (a2) and
+    // writes the coreness out (a6); only the control block is cleared here.
     cudaError_t e = record(g->ev[EV_R0], st, capture);
-    if (e == cudaSuccess && n)
-        e = cudaMemcpyAsync(g->est, g->est0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[0], 0xff, sizeof(uint32_t) * words, st);
-    if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[1], 0, sizeof(uint32_t) * words, st);
-    if (e == cudaSuccess && words) e = cudaMemsetAsync(g->bitmap[2], 0, sizeof(uint32_t) * words, st);
-    if (e == cudaSuccess) e = launch_ctl_init(g->ctl, g->tier_cnt, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl, 0, sizeof(SweepCtl), st);
     if (e != cudaSuccess) return cuda_status(e, "kcore_run init");
 
     SweepArgs a;
@@ -475,6 +470,9 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
     // refined rule unless KCORE_SIMPLE
     a.refined = sync_mode ? ((flags & KCORE_REFINED) ? 1 : 0) : ((flags & KCORE_SIMPLE) ? 0 : 1);
     a.off64 = g->csr.off_bytes == 8 ? 1 : 0;
+    a.est0 = g->est0;
+    for (int q = 0; q < kTiers; q++) a.init_cnt[q] = (unsigned)g->tier_cnt[q];
+    a.out = (flags & KCORE_OUT_DEVICE) ? coreness_out : (int*)g->est;
 
     // Grid: enough CTAs for the first sweep's work, at most the co-resident maximum.
     const long long work = n + g->csr.nnz;
@@ -487,13 +485,8 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
                          st, &g->last_grid);
     if (e == cudaSuccess) e = record(g->ev[EV_S1], st, capture);
     if (e != cudaSuccess) return cuda_status(e, "sweep launch");
-    if (flags & KCORE_OUT_DEVICE) {
-        e = launch_output(g->est, coreness_out, n, st);
-    } else {
-        e = launch_output(g->est, (int*)g->est, n, st);
-        if (e == cudaSuccess && n)
-            e = cudaMemcpyAsync(coreness_out, g->est, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-    }
+    if (!(flags & KCORE_OUT_DEVICE) && n)
+        e = cudaMemcpyAsync(coreness_out, g->est, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->hctl, g->ctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = record(g->ev[EV_R1], st, capture);
@@ -618,7 +611,8 @@ kcore_status kcore_stats(kcore_graph* g, kcore_run_stats* out) {
     out->entries_read = (int64_t)(c.tot[kAccDegsum] - c.tot[kAccSkipped]);
     out->decrease = (int64_t)c.tot[kAccDec];
     out->bytes_algorithmic = out->evaluated * (2LL * g->csr.off_bytes + 4) +
-                             8LL * out->entries_read + 4LL * out->updates;
+                             8LL * out->entries_read + 4LL * out->updates +
+                             16LL * out->n + 3LL * ((out->n + 31) / 32) * 4;  // a2 + a6
     out->grid = g->last_grid;
     cudaEventElapsedTime(&out->ms_sweep, g->ev[EV_S0], g->ev[EV_S1]);
     cudaEventElapsedTime(&out->ms_run, g->ev[EV_R0], g->ev[EV_R1]);

@@ -82,6 +82,10 @@ struct SweepArgs {
     int tail_max;
     int sync_mode, refined;
     int off64;
+    // Optional steps folded into the launch (null: done by the caller).
+    const uint32_t* est0;            // a2: est <- est0, F_0 = every vertex, with init_cnt per tier
+    unsigned init_cnt[kTiers];
+    int* out;                        // a6: out[v] = est[v] (coreness), at the end of the run
 };
 
 // Launch the persistent sweep kernel (cooperative launch).  `grid` 0 picks the

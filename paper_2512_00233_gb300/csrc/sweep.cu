@@ -1023,6 +1023,29 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
     if (tid < kAccN) s_acc[tid] = 0;
     __syncthreads();
 
+    const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    // a6 inside the launch: every CTA copies its share of the final estimates
+    auto write_out = [&]() {
+        if (a.out)
+            for (long long v = gtid; v < a.n; v += gstride) a.out[v] = (int)(est_load(a.est + v) & kEstMask);
+    };
+    // a2 inside the launch: estimates from the degrees, F_0 = every vertex
+    if (a.est0) {
+        for (long long v = gtid; v < a.n; v += gstride) a.est[v] = __ldg(a.est0 + v);
+        for (long long w = gtid; w < a.words; w += gstride) {
+            a.bitmap[0][w] = 0xffffffffu;
+            a.bitmap[1][w] = 0u;
+            a.bitmap[2][w] = 0u;
+        }
+        if (blockIdx.x == 0 && tid < kTiers) ctl->fcnt[0][tid] = a.init_cnt[tid];
+        if (multi) {
+            if (!grid_barrier(ctl, nbar, a.timeout_ns, &s_int[1])) return;
+        } else {
+            __syncthreads();
+        }
+    }
+
     for (;;) {
         const int cur = (int)(s % kSlots), nxt = (int)((s + 1) % kSlots);
         const int prv = (int)((s + kSlots - 1) % kSlots);
@@ -1093,6 +1116,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                 __threadfence();
                 atomicAdd(&ctl->tail_epoch, 1u);
             }
+            if (finished || capped || status != 0) write_out();
             return;
         }
 
@@ -1121,7 +1145,10 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                 const bool resume = s_int[1] != 0;
                 const long long rs = s_b[4];
                 __syncthreads();
-                if (!resume) return;
+                if (!resume) {  // the single-CTA tail ended the run
+                    write_out();
+                    return;
+                }
                 s = rs;
                 prev_tail = false;
                 continue;
