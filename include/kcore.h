@@ -237,6 +237,36 @@ kcore_status kcore_sweep_trace(kcore_graph* g, int64_t* frontier, int64_t* degsu
 kcore_status kcore_sweep_detail(kcore_graph* g, int64_t* entries_read, int64_t* decrease,
                                 int64_t cap, int64_t* count);
 
+/*
+ * kcore_run_from -- the iteration started from caller-given upper bounds
+ * instead of the degrees: dynamic core maintenance (Sec. VI names it as future
+ * work; this is its local-iteration form).  The fixed point reached from any
+ * pointwise upper bound of the coreness is the coreness (the operator is
+ * monotone and the coreness is its largest fixed point, Sec. III), so:
+ *   - after deleting edges (coreness can only drop): create the new graph and
+ *     pass the old coreness as `start` with the deleted edges' endpoints as
+ *     the frontier;
+ *   - after inserting b edges (each raises a coreness by at most 1): pass
+ *     old coreness + b as `start` and frontier = NULL (every vertex active).
+ *   start       n int32, start[v] >= core(v) required (not checked: a start
+ *               below the coreness gives a wrong result); values above the
+ *               degree are lowered to it, and such a vertex and its neighbours
+ *               join the frontier; negative values count as 0.
+ *   frontier    nfrontier vertex ids active at the start (repeats allowed), or
+ *               NULL for every vertex.  A vertex left out must satisfy
+ *               start[v] <= h-index of its neighbours' starts (true for the
+ *               old coreness where the neighbourhood did not change).  An id
+ *               out of [0, n) gives KCORE_ERR_INVALID.
+ *   flags       KCORE_IN_DEVICE (start and frontier are device pointers, read
+ *               on cuda_stream), KCORE_OUT_DEVICE, KCORE_SYNC_MODE,
+ *               KCORE_REFINED, KCORE_SIMPLE, KCORE_ASYNC as in kcore_run;
+ *               KCORE_GRAPH is refused (ERR_INVALID).
+ * Statistics and traces of the run are read as for kcore_run.
+ */
+kcore_status kcore_run_from(kcore_graph* g, const int32_t* start, const int32_t* frontier,
+                            int64_t nfrontier, int32_t* coreness_out, uint32_t flags,
+                            void* cuda_stream);
+
 /* Release a graph (waits for its outstanding work).  NULL is ignored. */
 void kcore_destroy(kcore_graph* g);
 

@@ -146,6 +146,39 @@ class Graph:
         self.last_status = st
         return out
 
+    def run_from(self, start, frontier=None, out=None, device: bool = True, sync_mode: bool = False,
+                 refined: bool | None = None, wait: bool = True, stream=None, check_status: bool = True):
+        """The iteration started from upper bounds `start` (n values >= the
+        coreness) with only `frontier` active (None: every vertex): dynamic
+        maintenance after edge deletions (old coreness, endpoints active) or
+        insertions (old coreness + number inserted, everything active).
+        `start` and `frontier` are both numpy arrays or both CUDA tensors."""
+        if refined is None:
+            refined = not sync_mode
+        ps, ks, ds = _ptr(start, np.int32)
+        pf, kf, df, nf = None, None, ds, 0
+        if frontier is not None:
+            pf, kf, df = _ptr(frontier, np.int32)
+            nf = int(kf.shape[0]) if hasattr(kf, "shape") else int(kf.numel())
+        if ds != df:
+            raise ValueError("start and frontier must both be host arrays or both CUDA tensors")
+        if out is None:
+            if device:
+                torch = _torch()
+                out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+            else:
+                out = np.empty(self.n, dtype=np.int32)
+        is_dev = _is_cuda_tensor(out)
+        optr = out.data_ptr() if is_dev else out.ctypes.data
+        flags = (KCORE_IN_DEVICE if ds else 0) | (KCORE_OUT_DEVICE if is_dev else 0) | \
+            (KCORE_SYNC_MODE if sync_mode else 0) | (KCORE_REFINED if refined and sync_mode else 0) | \
+            (KCORE_SIMPLE if not refined and not sync_mode else 0) | (0 if wait else KCORE_ASYNC)
+        st = lib().kcore_run_from(self._h, ps, pf, nf, optr, flags, _stream(stream))
+        if check_status:
+            check(st, "kcore_run_from")
+        self.last_status = st
+        return out
+
     def wait(self) -> int:
         return lib().kcore_wait(self._h)
 

@@ -90,6 +90,7 @@ SIGNATURES = {
     "kcore_stats": (c_i32, [c_vp, ctypes.POINTER(RunStats)]),
     "kcore_sweep_trace": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "kcore_sweep_detail": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
+    "kcore_run_from": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_u32, c_vp]),
     "kcore_destroy": (None, [c_vp]),
     "kcore_run_noalloc": (c_i32, [c_i64, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "kcore_default_serve_options": (None, [ctypes.POINTER(ServeOptions)]),

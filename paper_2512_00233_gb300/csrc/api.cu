@@ -425,8 +425,15 @@ cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
     return cudaEventRecordWithFlags(ev, st, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
+// Warm start of a run (kcore_run_from): device arrays, null for a cold start.
+struct WarmStart {
+    const int* start = nullptr;
+    const int* frontier = nullptr;
+    long long nf = 0;
+};
+
 kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, cudaStream_t st,
-                         bool capture) {
+                         bool capture, const WarmStart& warm = WarmStart()) {
     const int64_t n = g->csr.n;
     const bool sync_mode = (flags & KCORE_SYNC_MODE) != 0;
     const size_t words = (size_t)((n + 31) / 32);
@@ -472,6 +479,19 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
     a.off64 = g->csr.off_bytes == 8 ? 1 : 0;
     a.est0 = g->est0;
     for (int q = 0; q < kTiers; q++) a.init_cnt[q] = (unsigned)g->tier_cnt[q];
+    if (warm.start) {  // estimates and F_0 set up here instead of inside the launch
+        a.est0 = nullptr;
+        if (warm.frontier) a.init_list = nullptr;  // sweep 0 reads list[0]
+        if (words) {
+            e = cudaMemsetAsync(g->bitmap[0], warm.frontier ? 0 : 0xff, sizeof(uint32_t) * words, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(g->bitmap[1], 0, sizeof(uint32_t) * words, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(g->bitmap[2], 0, sizeof(uint32_t) * words, st);
+        }
+        if (e == cudaSuccess && !warm.frontier) e = launch_ctl_init(g->ctl, g->tier_cnt, st);
+        if (e == cudaSuccess)
+            e = launch_warm_init(a, g->csr.row_ptr, g->est0, warm.start, warm.frontier, warm.nf, st);
+        if (e != cudaSuccess) return cuda_status(e, "warm start");
+    }
     a.out = (flags & KCORE_OUT_DEVICE) ? coreness_out : (int*)g->est;
 
     // Grid: enough CTAs for the first sweep's work, at most the co-resident maximum.
@@ -556,6 +576,47 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
     kcore_status s = (flags & KCORE_GRAPH) ? graph_run(g, coreness_out, flags, st)
                                           : enqueue_run(g, coreness_out, flags, st, false);
     if (s != KCORE_OK) return s;
+    g->pending = true;
+    g->ran = true;
+    if (flags & KCORE_ASYNC) return KCORE_OK;
+    return wait_run(g);
+}
+
+kcore_status kcore_run_from(kcore_graph* g, const int32_t* start, const int32_t* frontier,
+                            int64_t nfrontier, int32_t* coreness_out, uint32_t flags,
+                            void* cuda_stream) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    const int64_t n = g->csr.n;
+    if (n > 0 && (!coreness_out || !start)) return fail(KCORE_ERR_INVALID, "start or coreness_out is NULL");
+    if (nfrontier < 0 || (nfrontier > 0 && !frontier))
+        return fail(KCORE_ERR_INVALID, "frontier is NULL or nfrontier < 0");
+    if (flags & KCORE_GRAPH) return fail(KCORE_ERR_INVALID, "KCORE_GRAPH is not available with a warm start");
+    if (g->pending) wait_run(g);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::string err;
+    if ((flags & KCORE_SYNC_MODE) && !g->upd_list) {
+        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
+        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
+        if (s != KCORE_OK) return fail(s, err);
+    }
+    WarmStart w;
+    int *tmp_start = nullptr, *tmp_front = nullptr;
+    kcore_status s = KCORE_OK;
+    if (flags & KCORE_IN_DEVICE) {
+        w.start = start;
+        w.frontier = frontier;
+    } else {
+        s = upload(start, (size_t)n, st, &tmp_start);
+        if (s == KCORE_OK && frontier) s = upload(frontier, (size_t)nfrontier, st, &tmp_front);
+        w.start = tmp_start;
+        w.frontier = frontier ? tmp_front : nullptr;
+    }
+    w.nf = frontier ? nfrontier : 0;
+    if (s == KCORE_OK && n > 0) s = enqueue_run(g, coreness_out, flags, st, false, w);
+    if (tmp_start) cudaFreeAsync(tmp_start, st);
+    if (tmp_front) cudaFreeAsync(tmp_front, st);
+    if (s != KCORE_OK) return s;
+    if (n == 0) return KCORE_OK;
     g->pending = true;
     g->ran = true;
     if (flags & KCORE_ASYNC) return KCORE_OK;

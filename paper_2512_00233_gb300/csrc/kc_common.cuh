@@ -90,6 +90,11 @@ struct SweepArgs {
 
 // Launch the persistent sweep kernel (cooperative launch).  `grid` 0 picks the
 // occupancy maximum; the grid used is returned.
+// Warm start of a run: estimates from `start` (capped at the degree) and, with
+// a frontier list, F_0 built in bitmap[0] / list[0] with counts in ctl.
+cudaError_t launch_warm_init(const SweepArgs& a, const void* row_ptr, const uint32_t* est0,
+                             const int* start, const int* frontier, long long nf, cudaStream_t st);
+cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cudaStream_t st);
 cudaError_t launch_sweep(const SweepArgs& a, int block, int grid_req, int ctas_per_sm,
                          cudaStream_t st, int* grid_used);
 

@@ -1392,6 +1392,67 @@ cudaError_t launch_sweep(const SweepArgs& a, int block, int grid_req, int ctas_p
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, sweep_smem_bytes(block), st);
 }
 
+// Warm start (dynamic maintenance): est[v] = tier bits | min(start[v], deg v).
+// With a frontier list, F_0 is that list plus every vertex the cap lowered
+// and its neighbours (a lowered estimate is a change its neighbours must
+// see), deduplicated by the F_0 bitmap and appended to list0 by tier; an id
+// out of range sets the status to KCORE_ERR_INVALID.  Without a list every
+// vertex is active and the caller sets up F_0.
+__device__ __forceinline__ void warm_activate(int v, const uint32_t* est0, uint32_t* bm0, int* list0,
+                                              const long long* tier_off, SweepCtl* ctl) {
+    const uint32_t bit = 1u << (v & 31);
+    if (atomicOr(bm0 + (v >> 5), bit) & bit) return;
+    const int t = (int)(__ldg(est0 + v) >> kEstBits);
+    const unsigned pos = atomicAdd(&ctl->fcnt[0][t], 1u);
+    list0[tier_off[t] + pos] = v;
+}
+
+template <typename Off>
+__global__ void k_warm_init(const Off* __restrict__ rp, const int* __restrict__ col, long long n,
+                            const uint32_t* __restrict__ est0, const int* __restrict__ start,
+                            uint32_t* __restrict__ est, const int* __restrict__ frontier, long long nf,
+                            uint32_t* bm0, int* list0, long long off0, long long off1, long long off2,
+                            SweepCtl* ctl) {
+    const long long tier_off[kTiers] = {off0, off1, off2};
+    const long long total = n > nf ? n : nf;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (frontier && i < nf) {
+            const int v = frontier[i];
+            if (v < 0 || v >= n) atomicCAS(&ctl->status, 0, (int)KCORE_ERR_INVALID);
+            else warm_activate(v, est0, bm0, list0, tier_off, ctl);
+        }
+        if (i < n) {
+            const uint32_t w0 = __ldg(est0 + i);
+            const uint32_t d = w0 & kEstMask;
+            const long long x = (long long)start[i];
+            const uint32_t e = x < 0 ? 0u : (x < (long long)d ? (uint32_t)x : d);
+            est[i] = (w0 & ~kEstMask) | e;
+            if (frontier && x > (long long)d) {  // lowered by the cap: v and its neighbours
+                warm_activate((int)i, est0, bm0, list0, tier_off, ctl);
+                for (long long j = (long long)rp[i]; j < (long long)rp[i + 1]; j++)
+                    warm_activate(__ldg(col + j), est0, bm0, list0, tier_off, ctl);
+            }
+        }
+    }
+}
+
+cudaError_t launch_warm_init(const SweepArgs& a, const void* row_ptr, const uint32_t* est0,
+                             const int* start, const int* frontier, long long nf, cudaStream_t st) {
+    const long long items = std::max<long long>({(long long)a.n, nf, 1LL});
+    const int g = (int)std::min<long long>((items + 255) / 256, 152LL * 32);
+    if (a.off64)
+        k_warm_init<<<g, 256, 0, st>>>((const long long*)row_ptr, a.col, a.n, est0, start, a.est,
+                                      frontier, nf, a.bitmap[0], a.list[0], a.tier_off[0],
+                                      a.tier_off[1], a.tier_off[2], a.ctl);
+    else
+        k_warm_init<<<g, 256, 0, st>>>((const int*)row_ptr, a.col, a.n, est0, start, a.est, frontier,
+                                      nf, a.bitmap[0], a.list[0], a.tier_off[0], a.tier_off[1],
+                                      a.tier_off[2], a.ctl);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(SweepCtl), st);
     if (e != cudaSuccess) return e;

@@ -16,7 +16,12 @@ relies on (readings H4/H5):
   vertex marks itself done once evaluated, and for a done vertex (or one not
   in the frontier) the refined test is applied to a value of est[v] read
   after seeing the mark (v's final value of the sweep);
-* applying the refined test to the value read before the mark is unsafe.
+* applying the refined test to the value read before the mark is unsafe;
+* warm starts (dynamic maintenance): after deleting edges, starting from the
+  old coreness with only the deleted edges' endpoints active, and after
+  inserting b edges, starting from old core + b with every vertex active, both
+  end at the new coreness.  A start above the degree is lowered to it, and
+  that vertex and its neighbours start active.
 """
 import random
 
@@ -31,9 +36,14 @@ def capped_hindex(vals, cap):
     return refimpl.hindex_sorted(vals, cap)
 
 
-def run_async(n, adj, rule, rng, max_sweeps=10_000):
-    est = [len(adj[v]) for v in range(n)]
-    frontier = set(range(n))
+def run_async(n, adj, rule, rng, max_sweeps=10_000, start=None, active=None):
+    est = [len(adj[v]) for v in range(n)] if start is None else \
+        [min(int(start[v]), len(adj[v])) for v in range(n)]
+    # a start above the degree is lowered to it: that vertex changed, so it
+    # and its neighbours start active
+    capped = set() if start is None else {v for v in range(n) if int(start[v]) > len(adj[v])}
+    frontier = set(range(n)) if active is None else set(active)
+    frontier |= capped | {w for v in capped for w in adj[v]}
     sweeps = 0
     while frontier:
         sweeps += 1
@@ -119,3 +129,35 @@ def test_unsafe_refined_variants_can_fail_in_place(rule):
             assert all(e >= c for e, c in zip(est, core))   # never below the coreness
             failures += est != core
     assert failures > 0
+
+
+def test_warm_starts_after_deletions_and_insertions():
+    rng = random.Random(31)
+    for trial in range(200):
+        n = rng.randint(3, 24)
+        adj = random_graph(rng, n, rng.uniform(0.15, 0.6))
+        core = coreness(n, adj)
+        edges = [(a, b) for a in range(n) for b in adj[a] if a < b]
+        # deletions: old coreness, endpoints active
+        gone = rng.sample(edges, min(len(edges), rng.randint(1, 4)))
+        adj2 = [set(x) for x in adj]
+        for a, b in gone:
+            adj2[a].discard(b)
+            adj2[b].discard(a)
+        adj2 = [sorted(x) for x in adj2]
+        ends = {a for a, _ in gone} | {b for _, b in gone}
+        for rule in ("simple", "refined_done"):
+            assert run_async(n, adj2, rule, rng, start=core, active=ends) == coreness(n, adj2), trial
+        # insertions: old coreness + b, everything active
+        missing = [(a, b) for a in range(n) for b in range(a + 1, n) if b not in adj[a]]
+        if not missing:
+            continue
+        new = rng.sample(missing, min(len(missing), rng.randint(1, 4)))
+        adj3 = [set(x) for x in adj]
+        for a, b in new:
+            adj3[a].add(b)
+            adj3[b].add(a)
+        adj3 = [sorted(x) for x in adj3]
+        start = [c + len(new) for c in core]
+        for rule in ("simple", "refined_done"):
+            assert run_async(n, adj3, rule, rng, start=start) == coreness(n, adj3), trial
