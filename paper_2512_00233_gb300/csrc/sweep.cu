@@ -790,12 +790,16 @@ __device__ __forceinline__ void hub_hist_pass(const SweepArgs& a, const int* col
 //   estimate stands and the pass stops, so a hub whose estimate holds reads
 //   only as much of its adjacency as it takes to find k supporters.
 //   Alongside, each thread counts min(x, k) by power-of-two class.
+//   Pass 1 also keeps an exact histogram of the values in the window
+//   [wl, k - 1], wl = max(k / 2, k - kHubBins).
 //   If c_k < k after the whole adjacency, h < k, and with N_m = #{min(x,k) >=
 //   2^m} the largest m* with N_m* >= 2^m* brackets h in
-//   [2^m*, min(2^(m*+1), k) - 1].  Pass 2 takes the histogram of the values in
-//   the bracket (buckets of one value, or coarse buckets and a further pass
-//   when the bracket is wider than kHubBins) and h is the last t with
-//   #{x >= t} >= t.  A last pass pushes the neighbours.
+//   [2^m*, min(2^(m*+1), k) - 1].  If the bracket starts inside the window, h
+//   is the last t of the window with c_k + #{window values >= t} >= t.
+//   Otherwise pass 2 takes the histogram of the values in the bracket
+//   (buckets of one value, or coarse buckets and a further pass when the
+//   bracket is wider than kHubBins) and h is the last t with #{x >= t} >= t.
+//   A last pass pushes the neighbours.
 template <typename Off>
 __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
                                            int u, uint32_t* s_pool, uint32_t* s_cls,
@@ -806,6 +810,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
     const int nw = T >> 5;
     uint32_t* s_lg = s_pool;
     uint32_t* s_hist = s_pool;
+    uint32_t* s_win = s_pool + kLogWords * T;  // pass 1's histogram of [wl, k - 1]
     const long long b = (long long)rp[u];
     const long long d = (long long)rp[u + 1] - b;
     const uint32_t w = est_load(a.est + u);
@@ -819,8 +824,15 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
         return;
     }
     const int* colb = a.col + b;
+    // values in the window [wl, k - 1] are also counted exactly in pass 1: a
+    // hub whose new estimate lands there (the usual case after the first
+    // sweep) needs no second pass.  The window stays above k / 2, away from
+    // the many small estimates of low-degree neighbours.
+    const int wl = max((k + 1) / 2, k - kHubBins);
+    const int nw_bins = k - wl;
 #pragma unroll
     for (int i = 0; i < kLogWords; i++) s_lg[i * T + tid] = 0;
+    for (int i = tid; i < nw_bins; i += T) s_win[i] = 0;
     if (tid < 32) s_cls[tid] = 0;
     if (tid == 0) s_hub[0] = 0;
     __syncthreads();
@@ -842,6 +854,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
                 const int m = 31 - __clz(y);
                 s_lg[(m >> 1) * T + tid] += 1u << ((m & 1) << 4);
             }
+            if (y >= wl && y < k) atomicAdd(&s_win[y - wl], 1u);
         }
         if ((c + 1) % kFoldChunks == 0) {  // keep the 16-bit counters from overflowing
 #pragma unroll
@@ -904,7 +917,11 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
     __syncthreads();
     const int ms = (int)s_hub[1];
     int h = 0;
-    if (ms >= 0) {
+    if (ms >= 0 && (1LL << ms) >= (long long)wl) {
+        // the bracket lies inside the window: pass 1's histogram decides
+        const int nt = hub_count_true(s_win, nw_bins, c_k, wl, 1, -1, s_u32, wsum, s_int);
+        h = wl + nt - 1;
+    } else if (ms >= 0) {
         long long lo = 1LL << ms;
         long long hi = (2 * lo < (long long)k ? 2 * lo : (long long)k) - 1;
         uint32_t above = 2 * lo <= (long long)k ? s_hub[2] : c_k;  // #{x >= hi + 1}
@@ -1339,12 +1356,12 @@ const void* pick_kernel(int t_lo, int off64) {
     return off64 ? (const void*)k_sweep<long long, 16> : (const void*)k_sweep<int, 16>;
 }
 
-// Dynamic shared memory of one CTA: push buffers, then the pool (the largest
-// of the CTA tier's counters, its histogram and every warp's kMedBig 16-bit
-// estimates).
+// Dynamic shared memory of one CTA: push buffers, then the pool (the larger
+// of the CTA tier's counters with its window histogram, and every warp's
+// kMedBig 16-bit estimates).
 size_t sweep_smem_bytes(int block) {
     const size_t nw = (size_t)block / 32;
-    const size_t pool = std::max<size_t>({(size_t)kLogWords * block, (size_t)kHubBins, nw * kMedSlice});
+    const size_t pool = std::max<size_t>({(size_t)kLogWords * block + kHubBins, nw * kMedSlice});
     static_assert((16 / 4) * 32 <= kMedSlice, "thread tier counts exceed a warp's slice");
     return sizeof(uint32_t) * (nw * kWCap + pool);
 }

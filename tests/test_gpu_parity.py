@@ -126,18 +126,26 @@ def test_launch_shapes_and_tiers_match_oracle(torch_cuda, opts, refined):
 
 @pytest.mark.parametrize("refined", [False, True])
 def test_hub_bracket_wider_than_histogram(torch_cuda, refined):
-    """A dense block whose coreness exceeds 8192: the power-of-two bracket
-    [8192, 16383] is wider than the 4096-bucket hub histogram, so the coarse
-    buckets and the fine pass both run."""
+    """A dense block whose coreness exceeds 8192, and a hub X joined to the
+    whole block and to 12,000 leaves.  In the first sweep X's estimate (its
+    degree, 20,600) is more than twice its new value (about the block's
+    coreness), so the value lies below pass 1's window and the power-of-two
+    bracket [8192, 16383] is wider than the 4096-bucket histogram: the coarse
+    buckets and the fine pass both run.  The block's own vertices land inside
+    the window."""
     rng = np.random.default_rng(1)
     k = 8600
     a, b = np.triu_indices(k, 1)
     keep = rng.random(a.shape[0]) < 0.99
-    n = k + 3000
-    src = np.concatenate([a[keep], rng.integers(0, n, 20000)]).astype(np.int32)
-    dst = np.concatenate([b[keep], rng.integers(0, n, 20000)]).astype(np.int32)
+    x = k
+    leaves = np.arange(k + 1, k + 1 + 12000)
+    n = k + 1 + 12000 + 3000
+    src = np.concatenate([a[keep], np.full(k, x), np.full(leaves.shape[0], x),
+                          rng.integers(0, n, 20000)]).astype(np.int32)
+    dst = np.concatenate([b[keep], np.arange(k), leaves,
+                          rng.integers(0, n, 20000)]).astype(np.int32)
     _, _, core = oracle_of(n, src, dst)
-    assert core.max() >= 8192
+    assert core.max() >= 8192 and 2 * core[x] < 20600
     got, _ = gpu_coreness(n, src, dst, refined=refined)
     np.testing.assert_array_equal(got, core)
 
