@@ -93,8 +93,9 @@ typedef struct kcore_options {
     int32_t  block;         /* threads per CTA of the sweep kernel, 64..512, x32     */
     int32_t  low_chunk;     /* thread tier: vertices per lane per work grab (1..8)   */
     int32_t  med_chunk;     /* warp tier: vertices per warp per work grab (1..64)    */
-    int32_t  tail_max;      /* frontier size at or below which one CTA continues
-                               (default 1024; negative disables the tail)          */
+    int32_t  tail_max;      /* frontier size at or below which one CTA continues,
+                               if it holds no vertex above t_hi and at most 16
+                               above t_lo (default 1024; negative disables)      */
     int32_t  ctas_per_sm;   /* persistent CTAs per SM (0 = occupancy maximum)        */
     int32_t  max_ctas;      /* cap on the persistent grid (0 = no cap)               */
     int64_t  max_sweeps;    /* sweep cap (0 = 2m + n + 1, a hard bound: every

@@ -38,9 +38,10 @@
 // cleared during sweep s.
 //
 // Sweeps are separated by a grid barrier; once a frontier is at most tail_max
-// vertices, CTA 0 continues alone with block barriers (the GPU analogue of
-// FastK's switch to sequential processing, Sec. IV) and the other CTAs wait,
-// to rejoin if the frontier grows again.  Every wait is bounded by timeout_ns
+// vertices with no CTA-tier and few warp-tier vertices, CTA 0 continues alone
+// with block barriers (the GPU analogue of FastK's switch to sequential
+// processing, Sec. IV) and the other CTAs wait, to rejoin if the frontier
+// grows again.  Every wait is bounded by timeout_ns
 // (globaltimer) and reports KCORE_ERR_TIMEOUT instead of hanging.
 //
 // Synchronous mode (KCORE_SYNC_MODE) follows Alg. 3: phase A computes new
@@ -61,6 +62,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlock = 512;
 constexpr int kMinBlocks = 2;
+constexpr int kTailMed = 16;        // warp-tier vertices a single-CTA tail sweep may hold
 constexpr int kMedR = 8;             // warp tier: up to 32 * kMedR neighbours
 
 __device__ __forceinline__ unsigned long long gtime_ns() {
@@ -1138,7 +1140,12 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
         }
 
         // ---- single-CTA tail transitions
-        if (multi && !tail && total <= a.tail_max && c2 == 0) {
+        // The tail is for frontiers that are small in work, not only in
+        // vertices: no CTA-tier vertex and at most kTailMed warp-tier ones
+        // (one CTA alone on a frontier of high-degree vertices would take
+        // milliseconds while the other CTAs wait).
+        const bool small = total <= a.tail_max && c1 <= (unsigned)kTailMed && c2 == 0;
+        if (multi && !tail && small) {
             // Every CTA has read this sweep's counts before CTA 0 goes on alone.
             if (!grid_barrier(ctl, nbar, a.timeout_ns, &s_int[1])) return;
             if (blockIdx.x != 0) {
@@ -1171,7 +1178,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                 continue;
             }
             tail = true;
-        } else if (multi && tail && total > 4LL * a.tail_max) {
+        } else if (multi && tail && (total > 4LL * a.tail_max || c1 > (unsigned)(4 * kTailMed) || c2 > 0)) {
             if (tid == 0) {  // hand the sweeps back to every CTA
                 ctl->resume_sweep = s;
                 ctl->tail_exit = 0;
