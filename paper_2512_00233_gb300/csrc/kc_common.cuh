@@ -69,7 +69,7 @@ struct SweepArgs {
     int* upd_val;                    // synchronous mode: their new (then old) values
     long long tier_off[kTiers];      // start of each tier inside a list
     SweepCtl* ctl;
-    long long* trace;                // [max_trace][4]: frontier, degsum, updates, start ns
+    long long* trace;                // [max_trace][kTraceCols]: see the kTr* columns
     long long max_trace;
     long long first_sweep;           // sweep index at which this launch starts
     long long max_sweeps;            // NOT_CONVERGED at this sweep index

@@ -112,7 +112,6 @@ __global__ void k_noalloc_bitmap(uint32_t* bm0, long long words, int n) {
 
 }  // namespace
 
-cudaError_t launch_output(const uint32_t* est, int* out, long long n, cudaStream_t st);
 
 }  // namespace kc
 
@@ -199,11 +198,11 @@ extern "C" kcore_status kcore_run_noalloc(int64_t n, const void* row_ptr, int32_
     a.med_chunk = o.med_chunk;
     a.tail_max = o.tail_max;
     a.off64 = row_ptr_bytes == 8 ? 1 : 0;
+    a.out = coreness_out;  // the estimates live there: the launch masks them to the coreness
     const long long want = std::max<long long>(1, (n + nnz + (long long)o.block * 32 - 1) /
                                                       ((long long)o.block * 32));
     int grid = 0;
     e = launch_sweep(a, o.block, (int)std::min<long long>(want, INT_MAX), 0, st, &grid);
-    if (e == cudaSuccess) e = launch_output(est, coreness_out, n, st);
     int h[2] = {0, 0};  // status, done
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h, &ctl->status, sizeof(int) * 2, cudaMemcpyDeviceToHost, st);

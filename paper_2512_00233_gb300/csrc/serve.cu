@@ -94,7 +94,6 @@ class Ranges {
         for (auto& kv : free_) b = std::max(b, kv.second);
         return b;
     }
-    long long used() const { return used_; }
     long long peak() const { return peak_; }
 
   private:

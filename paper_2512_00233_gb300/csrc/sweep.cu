@@ -1352,12 +1352,6 @@ __global__ void k_ctl_init(SweepCtl* ctl, unsigned c0, unsigned c1, unsigned c2)
     ctl->fcnt[0][2] = c2;
 }
 
-__global__ void k_output(const uint32_t* __restrict__ est, int* __restrict__ out, long long n) {
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x)
-        out[v] = (int)(__ldcg(est + v) & kEstMask);
-}
-
 const void* pick_kernel(int t_lo, int off64) {
     (void)t_lo;
     return off64 ? (const void*)k_sweep<long long, 16> : (const void*)k_sweep<int, 16>;
@@ -1486,12 +1480,5 @@ cudaError_t launch_ctl_init(SweepCtl* ctl, const long long tier_cnt[kTiers], cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_output(const uint32_t* est, int* out, long long n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int g = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
-    k_output<<<g, 256, 0, st>>>(est, out, n);
-    count_launch();
-    return cudaGetLastError();
-}
 
 }  // namespace kc
