@@ -32,7 +32,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kPad = 0xffffffffu;       // sorts after every vertex id
 constexpr int kSmallMax = 32, kMidMax = 1024, kBigMax = 16384;
-constexpr int kBigT = 1024;
+constexpr int kBigT = 512;
 
 // ------------------------------------------------------------------ scan
 constexpr int kScanT = 512, kScanI = 8, kScanTile = kScanT * kScanI;
@@ -385,6 +385,12 @@ __device__ __forceinline__ uint32_t warp_sort_row(uint32_t* seg, int len) {
     return total;
 }
 
+// Rows of 33..1024 entries, one warp each.  Two instantiations split by row
+// length (SHORT: up to 128), so that the many short rows do not run at the
+// register count (and occupancy) of the 32-value sorts of the long ones.
+constexpr int kMidShort = 128;
+
+template <bool SHORT>
 __global__ void k_sort_mid(const int* __restrict__ mid, const BuildCtl* bc,
                            const uint32_t* __restrict__ off, uint32_t* __restrict__ seg,
                            uint32_t* __restrict__ ucnt) {
@@ -395,57 +401,88 @@ __global__ void k_sort_mid(const int* __restrict__ mid, const BuildCtl* bc,
         const int u = mid[i];
         const uint32_t o = off[u];
         const int len = (int)(off[u + 1] - o);
+        if ((len <= kMidShort) != SHORT) continue;
         uint32_t c;
-        if (len <= 64) c = warp_sort_row<2>(seg + o, len);
-        else if (len <= 128) c = warp_sort_row<4>(seg + o, len);
-        else if (len <= 256) c = warp_sort_row<8>(seg + o, len);
-        else if (len <= 512) c = warp_sort_row<16>(seg + o, len);
-        else c = warp_sort_row<32>(seg + o, len);
+        if (SHORT) {
+            if (len <= 64) c = warp_sort_row<2>(seg + o, len);
+            else c = warp_sort_row<4>(seg + o, len);
+        } else {
+            if (len <= 256) c = warp_sort_row<8>(seg + o, len);
+            else if (len <= 512) c = warp_sort_row<16>(seg + o, len);
+            else c = warp_sort_row<32>(seg + o, len);
+        }
         if (lane == 0) ucnt[u] = c;
     }
 }
 
-// One CTA per row: bitonic sort in shared memory, then drop repeats.
+// One CTA per row of 1025..16384 entries: every warp sorts 1024-entry blocks
+// in registers (the warp bitonic sort), then log2(P / 1024) merge passes
+// between two shared-memory buffers, each thread producing a contiguous
+// stretch of the output after a merge-path search for its start; finally the
+// repeats are dropped.  P = the row length rounded up to a power of two,
+// padded with kPad.
 __global__ void __launch_bounds__(kBigT) k_sort_big(const int* __restrict__ big, const BuildCtl* bc,
                                                     const uint32_t* __restrict__ off,
                                                     uint32_t* __restrict__ seg,
                                                     uint32_t* __restrict__ ucnt) {
     extern __shared__ uint32_t sm[];
     __shared__ unsigned long long wtot;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kBigT >> 5;
     const unsigned nb = bc->n_big;
     for (unsigned r = blockIdx.x; r < nb; r += gridDim.x) {
         const int u = big[r];
         const uint32_t o = off[u];
         const int len = (int)(off[u + 1] - o);
-        int P = 1;
+        int P = 1024;
         while (P < len) P <<= 1;
-        for (int i = tid; i < P; i += kBigT) sm[i] = i < len ? seg[o + i] : kPad;
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int t = tid; t < P / 2; t += kBigT) {
-                    const int i = 2 * t - (t & (j - 1));
-                    const int l = i + j;
-                    const bool up = (i & k) == 0;
-                    const uint32_t a = sm[i], b = sm[l];
-                    if ((a > b) == up) {
-                        sm[i] = b;
-                        sm[l] = a;
-                    }
-                }
-                __syncthreads();
+        uint32_t* a = sm;
+        uint32_t* b = sm + kBigMax;
+        // 1024-entry blocks sorted by warps (blocked layout: lane holds 32 in a row)
+        for (int blk = wid; blk * 1024 < P; blk += nw) {
+            uint32_t x[32];
+#pragma unroll
+            for (int e = 0; e < 32; e++) {
+                const int i = blk * 1024 + lane * 32 + e;
+                x[e] = i < len ? seg[o + i] : kPad;
             }
+            warp_sort<32>(x);
+#pragma unroll
+            for (int e = 0; e < 32; e++) a[blk * 1024 + lane * 32 + e] = x[e];
+        }
+        __syncthreads();
+        // merge runs of width w into runs of 2w, a -> b, then swap
+        for (int w = 1024; w < P; w <<= 1) {
+            const int per = P / kBigT;
+            const int i0 = tid * per;                // first output index of this thread
+            const int base = i0 & ~(2 * w - 1);      // start of the pair of runs
+            const int i = i0 - base;                 // position inside the merged pair
+            const uint32_t* A = a + base;
+            const uint32_t* B = a + base + w;
+            int lo = max(0, i - w), hi = min(i, w);
+            while (lo < hi) {  // number of entries taken from A before position i
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] <= B[i - mid - 1]) lo = mid + 1;
+                else hi = mid;
+            }
+            int ia = lo, ib = i - lo;
+            for (int k = 0; k < per; k++) {
+                const bool fromA = ib >= w || (ia < w && A[ia] <= B[ib]);
+                b[i0 + k] = fromA ? A[ia++] : B[ib++];
+            }
+            __syncthreads();
+            uint32_t* t = a;
+            a = b;
+            b = t;
         }
         // keep flags over each thread's contiguous chunk, then a block scan
         const int per = (len + kBigT - 1) / kBigT;
-        const int i0 = min(len, tid * per), i1 = min(len, i0 + per);
+        const int j0 = min(len, tid * per), j1 = min(len, j0 + per);
         unsigned c = 0;
-        for (int i = i0; i < i1; i++) c += (i == 0 || sm[i] != sm[i - 1]) ? 1u : 0u;
+        for (int j = j0; j < j1; j++) c += (j == 0 || a[j] != a[j - 1]) ? 1u : 0u;
         unsigned long long tot;
         unsigned long long pos = block_excl_scan(c, &tot);
-        for (int i = i0; i < i1; i++)
-            if (i == 0 || sm[i] != sm[i - 1]) seg[o + pos++] = sm[i];
+        for (int j = j0; j < j1; j++)
+            if (j == 0 || a[j] != a[j - 1]) seg[o + pos++] = a[j];
         if (tid == 0) wtot = tot;
         __syncthreads();
         if (tid == 0) ucnt[u] = (uint32_t)wtot;
@@ -801,12 +838,14 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
         return KCORE_ERR_INVALID;
     }
     if (hbc.n_mid) {
-        k_sort_mid<<<grid_for((long long)hbc.n_mid * 32, 256), 256, 0, st>>>(mid, bc, off, seg, ucnt);
+        k_sort_mid<true><<<grid_for((long long)hbc.n_mid * 32, 256), 256, 0, st>>>(mid, bc, off, seg, ucnt);
+        count_launch();
+        k_sort_mid<false><<<grid_for((long long)hbc.n_mid * 32, 256), 256, 0, st>>>(mid, bc, off, seg, ucnt);
         count_launch();
         KC_TRY(cudaGetLastError(), "sort mid rows");
     }
     if (hbc.n_big) {
-        const size_t smem = sizeof(uint32_t) * kBigMax;
+        const size_t smem = sizeof(uint32_t) * 2 * kBigMax;  // two merge buffers
         KC_TRY(cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem), "smem attribute");
         k_sort_big<<<(unsigned)std::min<unsigned>(hbc.n_big, 152u * 2u), kBigT, smem, st>>>(
