@@ -83,7 +83,7 @@ typedef int32_t kcore_status;
  * override fields; 0 in a field means "library default".  The degree tiers
  * split the frontier by degree d: d <= t_lo is evaluated by one thread with a
  * register histogram, t_lo < d <= t_hi by one warp (estimates in registers up
- * to degree 256, staged in shared memory above), d > t_hi by one CTA with
+ * to degree 128, staged in shared memory above), d > t_hi by one CTA with
  * shared-memory counters.
  */
 typedef struct kcore_options {

@@ -63,7 +63,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlock = 512;
 constexpr int kMinBlocks = 2;
 constexpr int kTailMed = 16;        // warp-tier vertices a single-CTA tail sweep may hold
-constexpr int kMedR = 8;             // warp tier: up to 32 * kMedR neighbours
+constexpr int kMedR = 4;             // warp tier: up to 32 * kMedR neighbours in registers
 
 __device__ __forceinline__ unsigned long long gtime_ns() {
     unsigned long long t;
@@ -578,7 +578,7 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
 // x >= k; once that count reaches k the estimate stands and the pass stops.
 // Otherwise h < k is found by bisection on t with counts of y >= t taken from
 // shared memory, and a last pass pushes the neighbours with y > h.
-constexpr int kMedU = 8;
+constexpr int kMedU = 4;
 constexpr int kMedSlice = kMedBig / 2;  // words per warp
 
 template <typename Off>
