@@ -4,7 +4,8 @@ The GPU sweep updates estimates in place while other vertices of the same
 sweep read them, so a read may return the value a neighbour had when the sweep
 began or the one it has written since.  This replays sweeps with random
 evaluation orders and random stale reads and checks the claims the kernel
-relies on (readings H4/H5):
+relies on (the in-place activation rules and why the asynchronous fixed point
+is the coreness):
 
 * the simple rule (push v iff new_u < x, Sec. III-B) always ends at the
   coreness;
