@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--stream-count", type=int, default=1000)
+    ap.add_argument("--host-staging-gib", type=int, default=4,
+                    help="page-locked host staging of the batch engine (stream workload)")
     ap.add_argument("--arena-gib", type=int, default=8)
     ap.add_argument("--chunk-sweeps", type=int, default=16)
     ap.add_argument("--autotune", action="store_true",
@@ -474,13 +476,15 @@ def run_stream(args):
             m_total += gg.nnz // 2
         service.append(time.perf_counter() - a)
     t_one = time.perf_counter() - t0
-    opts = K.default_serve_options(mem_budget=args.arena_gib << 30, chunk_sweeps=args.chunk_sweeps)
+    opts = K.default_serve_options(mem_budget=args.arena_gib << 30, chunk_sweeps=args.chunk_sweeps,
+                                   host_staging=args.host_staging_gib << 30)
     # batched, saturated
     with K.BatchEngine(opts) as eng:
         for g in graphs[:3]:
             eng.poll(eng.submit_coo(g.n, g.src, g.dst), g.n, timeout_us=-1)
         t0 = time.perf_counter()
         tickets = [eng.submit_coo(g.n, g.src, g.dst) for g in graphs]
+        t_submit = time.perf_counter() - t0
         for g, t in zip(graphs, tickets):
             st, _ = eng.poll(t, g.n, timeout_us=-1)
             assert st == K.KCORE_OK
@@ -534,13 +538,16 @@ def run_stream(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "graph stream (n log-uniform 100..200000; ER/R-MAT/grid)",
                    "graphs": G, "m_total": m_total, "arena_gib": args.arena_gib,
+                   "host_staging_gib": args.host_staging_gib,
                    "chunk_sweeps": args.chunk_sweeps},
         "one_launch_per_graph": {"graphs_per_s": G / t_one,
                                  "p50_ms_at_served_rate": float(np.percentile(lat, 50)),
                                  "p99_ms_at_served_rate": float(np.percentile(lat, 99)),
                                  "mean_service_ms": 1e3 * float(np.mean(service))},
         "batched": {"graphs_per_s": rate_sat, "launches": sat["launches"], "sweeps": sat["sweeps"],
-                    "edges_per_s": m_total / t_batch},
+                    "edges_per_s": m_total / t_batch, "submit_s": t_submit,
+                    "busy_s": sat["busy_s"], "admit_s": sat["admit_s"], "sweep_s": sat["sweep_s"],
+                    "retire_s": sat["retire_s"], "admissions": sat["admissions"]},
         "served": {"arrival_rate_per_s": lam, "graphs_per_s": G / t_served,
                    "p50_ms": served["latency_p50_ms"], "p99_ms": served["latency_p99_ms"],
                    "launches": served["launches"]},

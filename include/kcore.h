@@ -322,6 +322,11 @@ typedef struct kcore_serve_options {
     int32_t  start_thread;    /* 1 = run the serving loop in a library thread;
                                  0 = caller drives it with kcore_batch_step           */
     kcore_options sweep;      /* sweep engine knobs (struct_size 0 = defaults)        */
+    int64_t  host_staging;    /* page-locked host bytes holding queued graphs' samples
+                                 and finished graphs' results, so that uploads and
+                                 result copies run asynchronously (0 = 1 GiB; < 0 =
+                                 none).  A graph that finds no room uses pageable
+                                 memory; results are the same either way.          */
 } kcore_serve_options;
 
 void kcore_default_serve_options(kcore_serve_options* opt);
@@ -367,6 +372,10 @@ typedef struct kcore_batch_stats {
     int64_t arena_bytes, arena_used_peak;
     double  latency_p50_ms, latency_p99_ms;   /* submit -> result ready, completed ones */
     double  busy_s;                  /* wall time the engine spent with work resident  */
+    double  admit_s, sweep_s, retire_s;  /* busy_s split by phase: admission (union
+                                            build, cleaning, placement), sweep
+                                            launches, retirement (result copies) */
+    int64_t admissions;              /* admission batches placed into the arena        */
 } kcore_batch_stats;
 
 kcore_status kcore_batch_stats_get(kcore_batch* b, kcore_batch_stats* out);

@@ -63,7 +63,7 @@ class RunStats(ctypes.Structure):
 class ServeOptions(ctypes.Structure):
     _fields_ = [("struct_size", c_u32), ("mem_budget", c_i64), ("max_slots", c_i32),
                 ("max_queue", c_i32), ("chunk_sweeps", c_i32), ("start_thread", c_i32),
-                ("sweep", Options)]
+                ("sweep", Options), ("host_staging", c_i64)]
 
 
 class BatchStats(ctypes.Structure):
@@ -71,7 +71,9 @@ class BatchStats(ctypes.Structure):
                 ("failed", c_i64), ("queued", c_i64), ("resident", c_i64),
                 ("launches", c_i64), ("sweeps", c_i64), ("arena_bytes", c_i64),
                 ("arena_used_peak", c_i64), ("latency_p50_ms", ctypes.c_double),
-                ("latency_p99_ms", ctypes.c_double), ("busy_s", ctypes.c_double)]
+                ("latency_p99_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("sweep_s", ctypes.c_double),
+                ("retire_s", ctypes.c_double), ("admissions", c_i64)]
 
 
 # name: (restype, argtypes)

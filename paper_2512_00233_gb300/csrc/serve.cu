@@ -103,13 +103,22 @@ class Ranges {
 
 struct Request {
     uint64_t ticket = 0;
-    int64_t n = 0;
-    std::vector<int32_t> src, dst;  // raw samples (a CSR input is expanded at submit)
+    int64_t n = 0, nnz = 0;
+    // raw samples (a CSR input is expanded at submit): sources at ps, targets
+    // at pd; either the two halves of one 2*nnz-word range of the page-locked
+    // staging pool (h_off >= 0) or the vectors
+    int32_t *ps = nullptr, *pd = nullptr;
+    long long h_off = -1;
+    std::vector<int32_t> src, dst;
     // state
     enum { QUEUED, RESIDENT, DONE } state = QUEUED;
     bool cancelled = false;
     kcore_status status = KCORE_OK;
-    std::vector<int32_t> result;
+    // the result as raw estimates (flag bits cleared when read): n words of the
+    // staging pool (r_off >= 0) or the vector
+    const uint32_t* res = nullptr;
+    long long r_off = -1;
+    std::vector<uint32_t> result;
     double t_submit = 0, t_done = 0;
     // placement
     int slot = -1;
@@ -174,6 +183,23 @@ __global__ void k_place(const Off* __restrict__ urp, const int* __restrict__ uco
     }
 }
 
+// The admission batch as one disjoint union of edge samples.  Graph g's raw
+// samples sit at raw[2 s_g, 2 s_g + c_g) (sources) and raw[2 s_g + c_g,
+// 2 s_{g+1}) (targets), s = sstart, c_g = s_{g+1} - s_g; its vertex ids move up
+// by vstart[g].
+__global__ void k_union(const int* __restrict__ raw, const long long* __restrict__ sstart,
+                        const long long* __restrict__ vstart, int ng, long long samples,
+                        int* __restrict__ us, int* __restrict__ ud) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < samples;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int g = slot_index(sstart, ng, j);  // empty graphs share their start
+        const long long s0 = sstart[g], c = sstart[g + 1] - s0, k = j - s0;
+        const int off = (int)vstart[g];
+        us[j] = raw[2 * s0 + k] + off;
+        ud[j] = raw[2 * s0 + c + k] + off;
+    }
+}
+
 // starts[i] <- row_ptr[starts[i]] (in place: one thread per boundary).
 __global__ void k_gather_rp(const long long* __restrict__ urp, const long long* starts, int count,
                             long long* out) {
@@ -220,6 +246,9 @@ struct kcore_batch {
     std::vector<int> h_slot_cnt;
     long long sweep = 0;  // next sweep index of the arena
     Ranges vr, er;
+    // page-locked host staging pool (int32 words, ranges guarded by mu)
+    int32_t* hpool = nullptr;
+    Ranges hr;
     // requests
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -234,8 +263,9 @@ struct kcore_batch {
     bool stop = false;
     std::mutex step_mu;  // one engine step at a time
     // statistics
-    long long submitted = 0, completed = 0, cancelled = 0, failed = 0, launches = 0, sweeps = 0;
-    double busy_s = 0;
+    long long submitted = 0, completed = 0, cancelled = 0, failed = 0, launches = 0, sweeps = 0,
+              admissions = 0;
+    double busy_s = 0, admit_s = 0, sweep_s = 0, retire_s = 0;
     std::vector<double> latencies;
 };
 
@@ -259,9 +289,92 @@ void batch_free(kcore_batch* b) {
         cudaStreamSynchronize(b->stream);
         cudaStreamDestroy(b->stream);
     }
+    if (b->hpool) cudaFreeHost(b->hpool);
     for (auto& kv : b->reqs) delete kv.second;
     delete b;
 }
+
+// Storage for a request's samples: a range of the staging pool when one is
+// free, else vectors.
+void stage_samples(kcore_batch* b, Request* r) {
+    long long at = -1;
+    if (b->hpool && r->nnz > 0) {
+        std::lock_guard<std::mutex> lk(b->mu);
+        at = b->hr.take(2 * r->nnz);
+    }
+    if (at >= 0) {
+        r->h_off = at;
+        r->ps = b->hpool + at;
+        r->pd = r->ps + r->nnz;
+    } else {
+        r->src.resize(r->nnz);
+        r->dst.resize(r->nnz);
+        r->ps = r->src.data();
+        r->pd = r->dst.data();
+    }
+}
+
+// Releases the samples' storage.  Called with b->mu held.
+void drop_samples(kcore_batch* b, Request* r) {
+    if (r->h_off >= 0) b->hr.give(r->h_off, 2 * r->nnz);
+    r->h_off = -1;
+    r->ps = r->pd = nullptr;
+    std::vector<int32_t>().swap(r->src);
+    std::vector<int32_t>().swap(r->dst);
+}
+
+// Releases the result's storage.  Called with b->mu held.
+void drop_result(kcore_batch* b, Request* r) {
+    if (r->r_off >= 0) b->hr.give(r->r_off, r->n);
+    r->r_off = -1;
+    r->res = nullptr;
+    std::vector<uint32_t>().swap(r->result);
+}
+
+// A request refused at submission.
+void discard(kcore_batch* b, Request* r) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    drop_samples(b, r);
+    delete r;
+}
+
+// to[i] = from[i]; returns the largest value read as unsigned, so a negative
+// id shows up as >= 2^31 (one pass: copy and range check together).
+uint32_t copy_max(int32_t* __restrict__ to, const int32_t* __restrict__ from, int64_t count) {
+    uint32_t m = 0;
+    for (int64_t i = 0; i < count; i++) {
+        const uint32_t v = (uint32_t)from[i];
+        to[i] = (int32_t)v;
+        m = v > m ? v : m;
+    }
+    return m;
+}
+
+// Host-to-device or device-to-host copies merged while both sides stay
+// contiguous.
+struct CopyRun {
+    cudaStream_t st;
+    cudaMemcpyKind kind;
+    char *dst = nullptr;
+    const char* src = nullptr;
+    size_t bytes = 0;
+    cudaError_t e = cudaSuccess;
+    void add(void* to, const void* from, size_t nb) {
+        if (nb == 0) return;
+        if (bytes && dst + bytes == (char*)to && src + bytes == (const char*)from) {
+            bytes += nb;
+            return;
+        }
+        flush();
+        dst = (char*)to;
+        src = (const char*)from;
+        bytes = nb;
+    }
+    void flush() {
+        if (bytes && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+        bytes = 0;
+    }
+};
 
 // Bytes of arena per vertex slot and per entry.
 constexpr long long kBytesPerVertex = 8 + 4 + 4 + kParities * kTiers * 4 + 1;
@@ -291,16 +404,35 @@ kcore_status retire(kcore_batch* b) {
             done.push_back(r);
         }
     }
-    for (Request* r : done) {
-        std::vector<uint32_t> raw(std::max<int64_t>(r->n, 1));
-        if (r->n)
-            e = cudaMemcpy(raw.data(), b->est + r->v0, sizeof(uint32_t) * r->n, cudaMemcpyDeviceToHost);
+    // results as raw estimates, into the staging pool where it has room (the
+    // copies then run asynchronously; graphs admitted together sit next to
+    // each other in the arena and usually in the pool, so their copies merge)
+    {
         std::lock_guard<std::mutex> lk(b->mu);
-        if (e != cudaSuccess) {
-            r->status = cuda_status(e, "batch result copy");
-        } else if (!r->cancelled) {
+        for (Request* r : done)
+            if (!r->cancelled && r->n > 0 && b->hpool) r->r_off = b->hr.take(r->n);
+    }
+    CopyRun cr{b->stream, cudaMemcpyDeviceToHost};
+    for (Request* r : done) {
+        if (r->cancelled || r->n == 0) continue;
+        uint32_t* to;
+        if (r->r_off >= 0) {
+            to = (uint32_t*)(b->hpool + r->r_off);
+        } else {
             r->result.resize(r->n);
-            for (int64_t i = 0; i < r->n; i++) r->result[i] = (int32_t)(raw[i] & kEstMask);
+            to = r->result.data();
+        }
+        r->res = to;
+        cr.add(to, b->est + r->v0, sizeof(uint32_t) * r->n);
+    }
+    cr.flush();
+    e = cr.e;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    for (Request* r : done) {
+        std::lock_guard<std::mutex> lk(b->mu);
+        if (e != cudaSuccess && !r->cancelled) {
+            r->status = cuda_status(e, "batch result copy");
+            drop_result(b, r);
         }
         b->vr.give(r->v0, r->vlen);
         b->er.give(r->e0, r->elen);
@@ -333,12 +465,13 @@ kcore_status admit(kcore_batch* b) {
             Request* r = b->queue.front();
             if (r->cancelled) {
                 b->queue.pop_front();
+                drop_samples(b, r);
                 r->state = Request::DONE;
                 b->cancelled++;
                 b->cv_done.notify_all();
                 continue;
             }
-            const long long v = r->n, ee = 2LL * (long long)r->src.size();
+            const long long v = r->n, ee = 2LL * r->nnz;
             if (vtot + v + 1 > vfree || etot + ee > efree) break;
             b->queue.pop_front();
             r->slot = b->free_slots.back();
@@ -346,48 +479,68 @@ kcore_status admit(kcore_batch* b) {
             batch.push_back(r);
             vtot += v;
             etot += ee;
-            samples += (long long)r->src.size();
+            samples += r->nnz;
         }
     }
     if (batch.empty()) return KCORE_OK;
     // the disjoint union of the batch, one spare vertex at the end
     const long long nu = vtot + 1;
-    std::vector<int32_t> us(samples), ud(samples);
-    std::vector<long long> gstart(batch.size() + 1);
-    std::vector<int> gslot(batch.size());
+    const int nb = (int)batch.size();
+    std::vector<long long> gstart(nb + 1), sstart(nb + 1);
+    std::vector<int> gslot(nb);
     long long vo = 0, so = 0;
-    for (size_t i = 0; i < batch.size(); i++) {
-        Request* r = batch[i];
+    for (int i = 0; i < nb; i++) {
         gstart[i] = vo;
-        gslot[i] = r->slot;
-        for (size_t j = 0; j < r->src.size(); j++) {
-            us[so + j] = (int32_t)(r->src[j] + vo);
-            ud[so + j] = (int32_t)(r->dst[j] + vo);
-        }
-        so += (long long)r->src.size();
-        vo += r->n;
+        sstart[i] = so;
+        gslot[i] = batch[i]->slot;
+        so += batch[i]->nnz;
+        vo += batch[i]->n;
     }
-    gstart[batch.size()] = vo;
+    gstart[nb] = vo;
+    sstart[nb] = so;
     std::string err;
     kcore_status s = KCORE_OK;
-    int *dsrc = nullptr, *dst_ = nullptr;
-    long long* dgs = nullptr;
+    int *raw = nullptr, *dsrc = nullptr, *dst_ = nullptr;
+    long long *dgs = nullptr, *dss = nullptr;
     int* dsl = nullptr;
     DevCsr csr;
     cudaStream_t st = b->stream;
-    cudaError_t e = pool_alloc((void**)&dsrc, sizeof(int) * std::max<long long>(samples, 1), st);
-    if (e == cudaSuccess) e = pool_alloc((void**)&dst_, sizeof(int) * std::max<long long>(samples, 1), st);
-    if (e == cudaSuccess) e = pool_alloc((void**)&dgs, sizeof(long long) * gstart.size(), st);
-    if (e == cudaSuccess) e = pool_alloc((void**)&dsl, sizeof(int) * gslot.size(), st);
-    if (e == cudaSuccess && samples)
-        e = cudaMemcpyAsync(dsrc, us.data(), sizeof(int) * samples, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && samples)
-        e = cudaMemcpyAsync(dst_, ud.data(), sizeof(int) * samples, cudaMemcpyHostToDevice, st);
+    const long long sm1 = std::max<long long>(samples, 1);
+    cudaError_t e = pool_alloc((void**)&raw, sizeof(int) * 2 * sm1, st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dsrc, sizeof(int) * sm1, st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dst_, sizeof(int) * sm1, st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dgs, sizeof(long long) * (nb + 1), st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dss, sizeof(long long) * (nb + 1), st);
+    if (e == cudaSuccess) e = pool_alloc((void**)&dsl, sizeof(int) * nb, st);
+    // each graph's samples as they were submitted (sources, then targets);
+    // staged graphs are contiguous in the pool and usually with each other
+    if (e == cudaSuccess) {
+        CopyRun cr{st, cudaMemcpyHostToDevice};
+        for (int i = 0; i < nb; i++) {
+            Request* r = batch[i];
+            int* at = raw + 2 * sstart[i];
+            if (r->h_off >= 0) {
+                cr.add(at, r->ps, sizeof(int) * 2 * r->nnz);
+            } else {
+                cr.add(at, r->ps, sizeof(int) * r->nnz);
+                cr.add(at + r->nnz, r->pd, sizeof(int) * r->nnz);
+            }
+        }
+        cr.flush();
+        e = cr.e;
+    }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dgs, gstart.data(), sizeof(long long) * gstart.size(),
-                            cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(dgs, gstart.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dsl, gslot.data(), sizeof(int) * gslot.size(), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(dss, sstart.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dsl, gslot.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && samples) {
+        const int g = (int)std::min<long long>((samples + 255) / 256, 152LL * 8);
+        k_union<<<g, 256, 0, st>>>(raw, dss, dgs, nb, samples, dsrc, dst_);
+        count_launch();
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) s = cuda_status(e, "batch admission copy");
     if (s == KCORE_OK) {
         s = clean_from_coo(nu, samples, dsrc, dst_, 8, st, &csr, &err);
@@ -411,7 +564,7 @@ kcore_status admit(kcore_batch* b) {
         const int cs = (int)(b->sweep % kSlots), pc = (int)(b->sweep % kParities);
         const int g = (int)std::min<long long>((nu + 256) / 256, 152LL * 16);
         k_place<long long><<<g, 256, 0, st>>>(
-            (const long long*)csr.row_ptr, csr.col, nu - 1, V0, E0, dgs, dsl, (int)batch.size(),
+            (const long long*)csr.row_ptr, csr.col, nu - 1, V0, E0, dgs, dsl, nb,
             b->opt.sweep.t_lo, b->opt.sweep.t_hi, b->rp, b->col, b->est, b->slot_of, b->list[pc],
             b->NV, b->bitmap[pc], b->ctl, cs);
         count_launch();
@@ -427,13 +580,17 @@ kcore_status admit(kcore_batch* b) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_status(e, "batch placement");
     }
+    cudaFreeAsync(raw, st);
     cudaFreeAsync(dsrc, st);
     cudaFreeAsync(dst_, st);
     cudaFreeAsync(dgs, st);
+    cudaFreeAsync(dss, st);
     cudaFreeAsync(dsl, st);
     dfree(csr.row_ptr, st);
     dfree(csr.col, st);
+    cudaStreamSynchronize(st);  // no upload from the samples' storage in flight
     std::lock_guard<std::mutex> lk(b->mu);
+    for (Request* r : batch) drop_samples(b, r);
     if (s != KCORE_OK) {
         if (V0 >= 0) b->vr.give(V0, nu);
         if (E0 >= 0) b->er.give(E0, std::max<long long>(csr.nnz, 1));
@@ -447,6 +604,7 @@ kcore_status admit(kcore_batch* b) {
         b->cv_done.notify_all();
         return s;
     }
+    b->admissions++;
     // per-graph ranges inside the block; the spare vertex and the block's
     // unused entry slack go with the last graph
     for (size_t i = 0; i < batch.size(); i++) {
@@ -519,14 +677,23 @@ kcore_status step(kcore_batch* b, int64_t* active) {
     cudaSetDevice(b->device);
     const double t0 = now_s();
     kcore_status s = admit(b);
+    const double t1 = now_s();
     bool any;
     {
         std::lock_guard<std::mutex> lk(b->mu);
         any = b->resident > 0;
     }
     if (s == KCORE_OK && any) s = run_chunk(b);
+    const double t2 = now_s();
     if (s == KCORE_OK && any) s = retire(b);
-    if (any) b->busy_s += now_s() - t0;
+    if (any) {
+        const double t3 = now_s();
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->busy_s += t3 - t0;
+        b->admit_s += t1 - t0;
+        b->sweep_s += t2 - t1;
+        b->retire_s += t3 - t2;
+    }
     if (active) {
         std::lock_guard<std::mutex> lk(b->mu);
         *active = b->resident + (int64_t)b->queue.size();
@@ -567,10 +734,12 @@ void engine_loop(kcore_batch* b) {
 kcore_status enqueue(kcore_batch* b, Request* r, uint64_t* ticket) {
     std::lock_guard<std::mutex> lk(b->mu);
     if ((long long)b->queue.size() >= b->opt.max_queue) {
+        drop_samples(b, r);
         delete r;
         return fail(KCORE_ERR_AGAIN, "batch queue is full");
     }
-    if (r->n + 1 > b->NV || 2LL * (long long)r->src.size() > b->NE) {
+    if (r->n + 1 > b->NV || 2LL * r->nnz > b->NE) {
+        drop_samples(b, r);
         delete r;
         return fail(KCORE_ERR_AGAIN, "graph can never fit the batch arena");
     }
@@ -598,6 +767,7 @@ void kcore_default_serve_options(kcore_serve_options* o) {
     o->chunk_sweeps = 16;
     o->start_thread = 1;
     kcore_default_options(&o->sweep);
+    o->host_staging = 1LL << 30;
 }
 
 kcore_status kcore_batch_create(const kcore_serve_options* opt, kcore_batch** out) {
@@ -614,6 +784,7 @@ kcore_status kcore_batch_create(const kcore_serve_options* opt, kcore_batch** ou
         if (opt->chunk_sweeps) o.chunk_sweeps = opt->chunk_sweeps;
         o.start_thread = opt->start_thread;
         if (opt->sweep.struct_size) o.sweep = opt->sweep;
+        if (opt->host_staging) o.host_staging = opt->host_staging;
     }
     kcore_options norm;
     kcore_status ns = normalize_options(&o.sweep, &norm);
@@ -670,6 +841,16 @@ kcore_status kcore_batch_create(const kcore_serve_options* opt, kcore_batch** ou
     for (int i = o.max_slots - 1; i >= 0; i--) b->free_slots.push_back(i);
     b->vr.reset(b->NV);
     b->er.reset(b->NE);
+    if (o.host_staging > 0) {
+        // the pool is an optimisation: without it copies use pageable memory
+        const long long words = o.host_staging / (long long)sizeof(int32_t);
+        if (cudaHostAlloc((void**)&b->hpool, sizeof(int32_t) * words, cudaHostAllocDefault) == cudaSuccess) {
+            b->hr.reset(words);
+        } else {
+            b->hpool = nullptr;
+            cudaGetLastError();
+        }
+    }
     if (o.start_thread) b->worker = std::thread(engine_loop, b);
     *out = b;
     return KCORE_OK;
@@ -683,13 +864,13 @@ kcore_status kcore_submit_coo(kcore_batch* b, int64_t n, int64_t nnz, const int3
         return fail(KCORE_ERR_INVALID, "bad graph arguments");
     Request* r = new Request();
     r->n = n;
-    r->src.assign(src, src + nnz);
-    r->dst.assign(dst, dst + nnz);
-    for (int64_t i = 0; i < nnz; i++)
-        if ((uint32_t)src[i] >= (uint64_t)n || (uint32_t)dst[i] >= (uint64_t)n) {
-            delete r;
-            return fail(KCORE_ERR_INVALID, "edge endpoint outside [0, n)");
-        }
+    r->nnz = nnz;
+    stage_samples(b, r);
+    const uint32_t hi = std::max(copy_max(r->ps, src, nnz), copy_max(r->pd, dst, nnz));
+    if (nnz > 0 && (uint64_t)hi >= (uint64_t)n) {
+        discard(b, r);
+        return fail(KCORE_ERR_INVALID, "edge endpoint outside [0, n)");
+    }
     return enqueue(b, r, ticket);
 }
 
@@ -707,22 +888,19 @@ kcore_status kcore_submit(kcore_batch* b, int64_t n, const void* row_ptr, int32_
         return fail(KCORE_ERR_INVALID, "row_ptr must start at 0 and end at nnz >= 0");
     Request* r = new Request();
     r->n = n;
-    r->src.resize(nnz);
-    r->dst.resize(nnz);
+    r->nnz = nnz;
+    stage_samples(b, r);
     for (int64_t u = 0; u < n; u++) {
         const int64_t lo = at(u), hi = at(u + 1);
         if (hi < lo || hi > nnz) {
-            delete r;
+            discard(b, r);
             return fail(KCORE_ERR_INVALID, "row_ptr must be non-decreasing");
         }
-        for (int64_t j = lo; j < hi; j++) {
-            if ((uint32_t)col_idx[j] >= (uint64_t)n) {
-                delete r;
-                return fail(KCORE_ERR_INVALID, "col_idx entry outside [0, n)");
-            }
-            r->src[j] = (int32_t)u;
-            r->dst[j] = col_idx[j];
-        }
+        for (int64_t j = lo; j < hi; j++) r->ps[j] = (int32_t)u;
+    }
+    if (nnz > 0 && (uint64_t)copy_max(r->pd, col_idx, nnz) >= (uint64_t)n) {
+        discard(b, r);
+        return fail(KCORE_ERR_INVALID, "col_idx entry outside [0, n)");
     }
     return enqueue(b, r, ticket);
 }
@@ -756,9 +934,13 @@ kcore_status kcore_poll(kcore_batch* b, uint64_t ticket, int32_t* coreness_out, 
         if (!ready()) return KCORE_PENDING;
     }
     kcore_status s = r->cancelled ? KCORE_ERR_CANCELLED : r->status;
-    if (s == KCORE_OK && coreness_out && r->n)
-        memcpy(coreness_out, r->result.data(), sizeof(int32_t) * r->n);
+    if (s == KCORE_OK && coreness_out && r->n) {
+        const uint32_t* raw = r->res;
+        for (int64_t i = 0; i < r->n; i++) coreness_out[i] = (int32_t)(raw[i] & kEstMask);
+    }
     b->reqs.erase(it);
+    drop_samples(b, r);
+    drop_result(b, r);
     delete r;
     if (s < 0) set_error(s == KCORE_ERR_CANCELLED ? "request was cancelled" : "request failed");
     return s;
@@ -795,6 +977,10 @@ kcore_status kcore_batch_stats_get(kcore_batch* b, kcore_batch_stats* out) {
     out->arena_bytes = b->NV * kBytesPerVertex + b->NE * kBytesPerEntry;
     out->arena_used_peak = b->vr.peak() * kBytesPerVertex + b->er.peak() * kBytesPerEntry;
     out->busy_s = b->busy_s;
+    out->admit_s = b->admit_s;
+    out->sweep_s = b->sweep_s;
+    out->retire_s = b->retire_s;
+    out->admissions = b->admissions;
     if (!b->latencies.empty()) {
         std::vector<double> l = b->latencies;
         std::sort(l.begin(), l.end());

@@ -49,6 +49,7 @@ def test_defaults_and_version():
     assert "sm_103a" in K.version()
     s = K.default_serve_options()
     assert s.struct_size == ctypes.sizeof(K.ServeOptions)
+    assert s.host_staging == 1 << 30
 
 
 def test_struct_layout_matches_header(tmp_path):

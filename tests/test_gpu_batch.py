@@ -30,9 +30,12 @@ def alone(g):
         return gg.run(device=False)
 
 
-def test_batch_results_match_oracle_and_alone():
+@pytest.mark.parametrize("staging", [0, 1 << 18, -1])
+def test_batch_results_match_oracle_and_alone(staging):
+    """staging: the default page-locked pool; one that holds only some of the
+    graphs (the rest use pageable memory, mixed within one admission); none."""
     graphs = stream(40, 20000, seed=3)
-    opts = K.default_serve_options(mem_budget=256 << 20, chunk_sweeps=4)
+    opts = K.default_serve_options(mem_budget=256 << 20, chunk_sweeps=4, host_staging=staging)
     with K.BatchEngine(opts) as eng:
         tickets = [eng.submit_coo(g.n, g.src, g.dst) for g in graphs]
         for g, t in zip(graphs, tickets):
