@@ -101,6 +101,13 @@ typedef struct kcore_options {
     int64_t  max_sweeps;    /* sweep cap (0 = 2m + n + 1, a hard bound: every
                                productive sweep lowers the sum of estimates)       */
     double   timeout_s;     /* budget of every bounded device wait (default 20 s)   */
+    int32_t  build_sort;    /* cleaning of raw edge samples (kcore_create_coo and
+                               batches): 1 = one radix sort of all entries;
+                               -1 = rows counted, filled and sorted one by one;
+                               0 (default) = the sort when the input has at least
+                               2^18 samples, 2*samples >= 8n, and rows of more
+                               than 32 entries hold half of the entries or more.
+                               The cleaned graph is the same either way.          */
 } kcore_options;
 
 /* Fill `opt` with the defaults. */

@@ -46,6 +46,7 @@ kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
     if (in->max_ctas) out->max_ctas = in->max_ctas;
     if (in->max_sweeps) out->max_sweeps = in->max_sweeps;
     if (in->timeout_s > 0) out->timeout_s = in->timeout_s;
+    if (in->build_sort) out->build_sort = in->build_sort;
     if (out->t_lo < 1 || out->t_lo > 32) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..32");
     if (out->t_hi < out->t_lo || out->t_hi > kMedBig)
         return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..2048");
@@ -56,6 +57,8 @@ kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
     if (out->med_chunk < 1 || out->med_chunk > 64) return fail(KCORE_ERR_INVALID, "med_chunk 1..64");
     if (out->max_sweeps < 0 || out->ctas_per_sm < 0 || out->max_ctas < 0)
         return fail(KCORE_ERR_INVALID, "negative option");
+    if (out->build_sort < -1 || out->build_sort > 1)
+        return fail(KCORE_ERR_INVALID, "build_sort must be -1, 0 or 1");
     return KCORE_OK;
 }
 
@@ -81,6 +84,7 @@ struct kcore_graph {
     SweepCtl* hctl = nullptr;  // pinned copy of the control block after a run
     TierOut* htier = nullptr;  // pinned copy of the tier split results (same block)
     TierOut* dtier = nullptr;  // device tier split results
+    void* state = nullptr;     // one block holding est0 .. dtier above
     cudaEvent_t ev[6] = {};    // create0, create1, run0, sweep0, sweep1, run1
     bool pending = false;
     bool ran = false;
@@ -109,18 +113,9 @@ void release(kcore_graph* g) {
     cudaDeviceSynchronize();
     dfree(g->csr.row_ptr);
     dfree(g->csr.col);
-    dfree(g->est0);
-    dfree(g->est);
-    dfree(g->init_list);
-    for (int p = 0; p < kParities; p++) {
-        dfree(g->list[p]);
-        dfree(g->bitmap[p]);
-    }
+    dfree(g->state);  // est0, est, lists, bitmaps, ctl, trace, dtier
     dfree(g->upd_list);
     dfree(g->upd_val);
-    dfree(g->ctl);
-    dfree(g->trace);
-    dfree(g->dtier);
     if (g->hctl) pinned_put(g->hctl);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
@@ -155,24 +150,30 @@ kcore_status finish_graph(kcore_graph* g, cudaStream_t st) {
     std::string err;
     const int64_t n = g->csr.n;
     const size_t words = (size_t)((n + 31) / 32);
-    kcore_status s;
-#define KC_ALLOC(ptr, bytes)                                    \
-    do {                                                        \
-        s = dmalloc((void**)&(ptr), (bytes), &err, st);         \
-        if (s != KCORE_OK) return fail(s, err);                 \
-    } while (0)
-    KC_ALLOC(g->est0, sizeof(uint32_t) * n);
-    KC_ALLOC(g->est, sizeof(uint32_t) * n);
-    KC_ALLOC(g->init_list, sizeof(int) * n);
-    for (int p = 0; p < kParities; p++) {
-        KC_ALLOC(g->list[p], sizeof(int) * n);
-        KC_ALLOC(g->bitmap[p], sizeof(uint32_t) * words);
-    }
-    KC_ALLOC(g->ctl, sizeof(SweepCtl));
     g->max_trace = 1 << 16;
-    KC_ALLOC(g->trace, sizeof(long long) * kTraceCols * g->max_trace);
-    KC_ALLOC(g->dtier, sizeof(TierOut));
-#undef KC_ALLOC
+    // one allocation, carved into 256-byte aligned arrays
+    auto rnd = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
+    const size_t vec = rnd(sizeof(uint32_t) * n), bm = rnd(sizeof(uint32_t) * words);
+    const size_t total = (3 + kParities) * vec + kParities * bm + rnd(sizeof(SweepCtl)) +
+                         rnd(sizeof(long long) * kTraceCols * g->max_trace) + rnd(sizeof(TierOut));
+    kcore_status s = dmalloc(&g->state, total, &err, st);
+    if (s != KCORE_OK) return fail(s, err);
+    char* at = (char*)g->state;
+    auto take = [&](size_t b) {
+        char* p = at;
+        at += b;
+        return p;
+    };
+    g->est0 = (uint32_t*)take(vec);
+    g->est = (uint32_t*)take(vec);
+    g->init_list = (int*)take(vec);
+    for (int p = 0; p < kParities; p++) {
+        g->list[p] = (int*)take(vec);
+        g->bitmap[p] = (uint32_t*)take(bm);
+    }
+    g->ctl = (SweepCtl*)take(rnd(sizeof(SweepCtl)));
+    g->trace = (long long*)take(rnd(sizeof(long long) * kTraceCols * g->max_trace));
+    g->dtier = (TierOut*)take(rnd(sizeof(TierOut)));
     static_assert(sizeof(SweepCtl) <= 2048 && sizeof(TierOut) <= kPinnedBlock - 2048,
                   "pinned block layout");
     cudaError_t e = pinned_get((void**)&g->hctl, kPinnedBlock);
@@ -265,6 +266,7 @@ void kcore_default_options(kcore_options* o) {
     o->max_ctas = 0;
     o->max_sweeps = 0;
     o->timeout_s = 20.0;
+    o->build_sort = 0;
 }
 
 const char* kcore_last_error(void) { return t_err.c_str(); }
@@ -295,7 +297,8 @@ kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const 
     }
     std::string err;
     if (s == KCORE_OK) {
-        s = clean_from_coo(n, nnz, ds, dd, row_ptr_bytes, st, &g->csr, &err);
+        s = clean_from_coo(n, nnz, ds, dd, row_ptr_bytes, g->opt.build_sort, st, &g->csr,
+                           &err);
         if (s != KCORE_OK) set_error(err);
     }
     if (tmp_s) cudaFreeAsync(tmp_s, st);

@@ -1,25 +1,34 @@
 // Device CSR cleaning (Sec. IV-A: graphs treated as undirected, self-loops
 // removed; Sec. III-B: neighbour lists kept as sorted vectors).
 //
-// Pipeline, all on the device:
+// Two pipelines give the same CSR, all on the device.
+//
+// Counted (raw CSR input, and edge samples whose rows are mostly short):
 //   1. count    every sample (u, v) with u != v adds one to deg(u) and deg(v)
 //               (atomics); ids outside [0, n) raise a flag and are skipped.
-//   2. offsets  exclusive scan of the counts: the segment of each row.
+//   2. offsets  exclusive scan of the counts: the segment of each row; the
+//               rows longer than 32 entries are listed by size class and the
+//               classes copied to the host while steps 3-4 run.
 //   3. scatter  each sample writes v into u's segment and u into v's, at a slot
 //               taken with an atomic on the row's fill counter (unordered).
 //   4. sort     each segment is sorted and its repeats dropped in place, by a
 //               size class: one thread with a register sorting network (<= 32
 //               entries), one warp with a register bitonic sort (<= 1024), one
-//               CTA with a shared-memory bitonic sort (<= 16384), and, for the
-//               few larger hub rows, a stable LSD radix sort of 64-bit
+//               CTA with shared-memory merges (<= 16384), and, for the few
+//               larger hub rows, a stable LSD radix sort of 64-bit
 //               (row rank, column) keys over the whole GPU.
 //   5. rows     exclusive scan of the distinct counts gives row_ptr; the
 //               sorted distinct prefixes are copied into col_idx.
-// The host waits three times: for the entry count, for the size classes, and
-// at the end for the sizes.
+//
+// Sorted (edge samples where rows of more than 32 entries hold most entries):
+// both directed entries of every sample become a 64-bit (row, column) key;
+// one LSD radix sort over the row and column bits orders them; a pass drops
+// repeats and writes col_idx and the row counts; a scan gives row_ptr.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -33,6 +42,47 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kPad = 0xffffffffu;       // sorts after every vertex id
 constexpr int kSmallMax = 32, kMidMax = 1024, kBigMax = 16384;
 constexpr int kBigT = 512;
+constexpr long long kSortAutoSamples = 1 << 18, kSortAutoDegree = 8;
+constexpr int kSortProbe = 16;
+
+// ------------------------------------------------------------------ temporaries
+// The temporaries of one call, freed together (stream-ordered) when it ends.
+// reserve() takes one block from the pool and get() carves 256-byte aligned
+// arrays from it, so that a call makes a few allocations instead of one per
+// array; a request that does not fit the block gets its own allocation.
+struct Temp {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    explicit Temp(cudaStream_t s) : st(s) {}
+    ~Temp() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+    static size_t round(size_t bytes) { return (std::max<size_t>(bytes, 1) + 255) & ~size_t(255); }
+    cudaError_t reserve(size_t bytes) {
+        char* b = nullptr;
+        cudaError_t e = pool_alloc((void**)&b, bytes, st);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(b);
+        base = b;
+        cap = bytes;
+        used = 0;
+        return cudaSuccess;
+    }
+    template <typename T>
+    cudaError_t get(T** p, size_t count) {
+        const size_t bytes = round(std::max<size_t>(count, 1) * sizeof(T));
+        if (base && used + bytes <= cap) {
+            *p = reinterpret_cast<T*>(base + used);
+            used += bytes;
+            return cudaSuccess;
+        }
+        cudaError_t e = pool_alloc((void**)p, bytes, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
 
 // ------------------------------------------------------------------ scan
 constexpr int kScanT = 512, kScanI = 8, kScanTile = kScanT * kScanI;
@@ -108,12 +158,96 @@ struct ReadU32 {
     __device__ unsigned long long operator()(long long i) const { return p[i]; }
 };
 
+template <typename Out>
+cudaError_t exclusive_scan4(const uint32_t* in, long long N, Out* out, bool with_total, cudaStream_t st,
+                            Temp* tmp);
+
+// Block sums and their offsets of one scan level (from `tmp` when given).
+inline cudaError_t scan_scratch(long long nb, unsigned long long** bsum, unsigned long long** boff,
+                                cudaStream_t st, Temp* tmp) {
+    if (tmp) {
+        cudaError_t e = tmp->get(bsum, (size_t)nb);
+        return e == cudaSuccess ? tmp->get(boff, (size_t)nb + 1) : e;
+    }
+    cudaError_t e = pool_alloc((void**)bsum, sizeof(unsigned long long) * nb, st);
+    if (e != cudaSuccess) return e;
+    e = pool_alloc((void**)boff, sizeof(unsigned long long) * (nb + 1), st);
+    if (e != cudaSuccess) cudaFreeAsync(*bsum, st);
+    return e;
+}
+inline void scan_scratch_free(unsigned long long* bsum, unsigned long long* boff, cudaStream_t st,
+                              Temp* tmp) {
+    if (tmp) return;
+    cudaFreeAsync(bsum, st);
+    cudaFreeAsync(boff, st);
+}
+
+// 32-bit inputs with 16-byte aligned arrays: each thread takes 4 consecutive
+// elements in one 16-byte access, so a warp reads (and writes) contiguous
+// bytes instead of every lane striding through its own chunk.
+constexpr int kVecT = 512, kVecTile = kVecT * 4;
+
+__device__ __forceinline__ uint4 load4(const uint32_t* p, long long i, long long N) {
+    if (i + 4 <= N) return *reinterpret_cast<const uint4*>(p + i);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (i < N) v.x = p[i];
+    if (i + 1 < N) v.y = p[i + 1];
+    if (i + 2 < N) v.z = p[i + 2];
+    return v;
+}
+
+template <typename Out>
+__device__ __forceinline__ void store4(Out* out, long long i, long long N, unsigned long long a,
+                                      unsigned long long b, unsigned long long c,
+                                      unsigned long long d) {
+    if (i + 4 <= N) {
+        if constexpr (sizeof(Out) == 4) {
+            *reinterpret_cast<uint4*>(out + i) = make_uint4((uint32_t)a, (uint32_t)b, (uint32_t)c, (uint32_t)d);
+        } else {
+            *reinterpret_cast<ulonglong2*>(out + i) = make_ulonglong2(a, b);
+            *reinterpret_cast<ulonglong2*>(out + i + 2) = make_ulonglong2(c, d);
+        }
+        return;
+    }
+    if (i < N) out[i] = (Out)a;
+    if (i + 1 < N) out[i + 1] = (Out)b;
+    if (i + 2 < N) out[i + 2] = (Out)c;
+}
+
+__global__ void __launch_bounds__(kVecT) k_scan_reduce4(const uint32_t* __restrict__ in, long long N,
+                                                        unsigned long long* bsum) {
+    const uint4 v = load4(in, (long long)blockIdx.x * kVecTile + threadIdx.x * 4, N);
+    unsigned long long tot;
+    block_excl_scan((unsigned long long)v.x + v.y + v.z + v.w, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+template <typename Out>
+__global__ void __launch_bounds__(kVecT) k_scan_down4(const uint32_t* __restrict__ in, long long N,
+                                                      const unsigned long long* boff, Out* out,
+                                                      int write_total) {
+    const long long i = (long long)blockIdx.x * kVecTile + threadIdx.x * 4;
+    const uint4 v = load4(in, i, N);
+    unsigned long long tot;
+    const unsigned long long b0 = boff ? boff[blockIdx.x] : 0ull;
+    const unsigned long long r0 = block_excl_scan((unsigned long long)v.x + v.y + v.z + v.w, &tot) + b0;
+    store4(out, i, N, r0, r0 + v.x, r0 + v.x + v.y, r0 + v.x + v.y + v.z);
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1)
+        out[N] = (Out)(b0 + tot);
+}
+
 // out[0..N) = exclusive prefix sums of f(0..N); out[N] = total if with_total.
+// Scratch comes from `tmp` when given (no allocation of its own).
 template <typename F, typename Out>
-cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStream_t st) {
+cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStream_t st,
+                           Temp* tmp = nullptr) {
     if (N <= 0) {
         if (with_total) return cudaMemsetAsync(out, 0, sizeof(Out), st);
         return cudaSuccess;
+    }
+    if constexpr (std::is_same<F, ReadU32>::value) {
+        if ((reinterpret_cast<uintptr_t>(f.p) | reinterpret_cast<uintptr_t>(out)) % 16 == 0)
+            return exclusive_scan4(f.p, N, out, with_total, st, tmp);
     }
     const long long nb = (N + kScanTile - 1) / kScanTile;
     if (nb == 1) {
@@ -123,25 +257,56 @@ cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStre
         return cudaGetLastError();
     }
     unsigned long long *bsum = nullptr, *boff = nullptr;
-    cudaError_t e = pool_alloc((void**)&bsum, sizeof(unsigned long long) * nb, st);
+    cudaError_t e = scan_scratch(nb, &bsum, &boff, st, tmp);
     if (e != cudaSuccess) return e;
-    e = pool_alloc((void**)&boff, sizeof(unsigned long long) * (nb + 1), st);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(bsum, st);
-        return e;
-    }
     k_scan_reduce<<<(unsigned)nb, kScanT, 0, st>>>(f, N, bsum);
     count_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = exclusive_scan(ReadU64{bsum}, nb, boff, false, st);
+    if (e == cudaSuccess) e = exclusive_scan(ReadU64{bsum}, nb, boff, false, st, tmp);
     if (e == cudaSuccess) {
         k_scan_down<<<(unsigned)nb, kScanT, 0, st>>>(f, N, boff, out, with_total ? 1 : 0);
         count_launch();
         e = cudaGetLastError();
     }
-    cudaFreeAsync(bsum, st);
-    cudaFreeAsync(boff, st);
+    scan_scratch_free(bsum, boff, st, tmp);
     return e;
+}
+
+template <typename Out>
+cudaError_t exclusive_scan4(const uint32_t* in, long long N, Out* out, bool with_total, cudaStream_t st,
+                            Temp* tmp) {
+    const long long nb = (N + kVecTile - 1) / kVecTile;
+    if (nb == 1) {
+        k_scan_down4<<<1, kVecT, 0, st>>>(in, N, (const unsigned long long*)nullptr, out,
+                                          with_total ? 1 : 0);
+        count_launch();
+        return cudaGetLastError();
+    }
+    unsigned long long *bsum = nullptr, *boff = nullptr;
+    cudaError_t e = scan_scratch(nb, &bsum, &boff, st, tmp);
+    if (e != cudaSuccess) return e;
+    k_scan_reduce4<<<(unsigned)nb, kVecT, 0, st>>>(in, N, bsum);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = exclusive_scan(ReadU64{bsum}, nb, boff, false, st, tmp);
+    if (e == cudaSuccess) {
+        k_scan_down4<<<(unsigned)nb, kVecT, 0, st>>>(in, N, boff, out, with_total ? 1 : 0);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    scan_scratch_free(bsum, boff, st, tmp);
+    return e;
+}
+
+// Scratch bytes an exclusive scan of N 32-bit elements takes from a Temp.
+size_t scan_scratch_bytes(long long N) {
+    size_t b = 0;
+    long long nb = (N + kVecTile - 1) / kVecTile;
+    while (nb > 1) {
+        b += Temp::round(sizeof(unsigned long long) * nb) + Temp::round(sizeof(unsigned long long) * (nb + 1));
+        nb = (nb + kScanTile - 1) / kScanTile;
+    }
+    return b;
 }
 
 // ------------------------------------------------------------------ count / scatter
@@ -151,12 +316,14 @@ struct BuildCtl {
     int bad;               // an id or offset out of range
     unsigned n_mid, n_big, n_huge;
     unsigned long long huge_entries;
+    unsigned long long entries, heavy;  // all counted entries; those in rows above kSmallMax
 };
 
+// Every step-th sample (step 1: all of them).
 __global__ void k_count_coo(const int* __restrict__ src, const int* __restrict__ dst, long long S,
-                            int n, uint32_t* __restrict__ cnt, BuildCtl* bc) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
-         i += (long long)gridDim.x * blockDim.x) {
+                            int n, uint32_t* __restrict__ cnt, BuildCtl* bc, int step) {
+    for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * step; i < S;
+         i += (long long)gridDim.x * blockDim.x * step) {
         const int s = src[i], d = dst[i];
         if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n) {
             bc->bad = 1;
@@ -165,6 +332,26 @@ __global__ void k_count_coo(const int* __restrict__ src, const int* __restrict__
         if (s == d) continue;
         atomicAdd(&cnt[s], 1u);
         atomicAdd(&cnt[d], 1u);
+    }
+}
+
+// Entries in rows of more than `limit` entries, and all entries.
+__global__ void k_heavy(const uint32_t* __restrict__ cnt, long long n, uint32_t limit, BuildCtl* bc) {
+    unsigned long long all = 0, heavy = 0;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[u];
+        all += c;
+        heavy += c > limit ? c : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        all += __shfl_down_sync(kFull, all, o);
+        heavy += __shfl_down_sync(kFull, heavy, o);
+    }
+    if ((threadIdx.x & 31) == 0 && all) {
+        atomicAdd(&bc->entries, all);
+        atomicAdd(&bc->heavy, heavy);
     }
 }
 
@@ -284,8 +471,7 @@ __device__ __forceinline__ uint32_t thread_sort_row(uint32_t* seg, int len) {
 
 // Rows of at most 32 entries are sorted here; larger ones are listed by class.
 __global__ void k_sort_small(int n, const uint32_t* __restrict__ off, uint32_t* __restrict__ seg,
-                             uint32_t* __restrict__ ucnt, int* __restrict__ mid, int* __restrict__ big,
-                             int* __restrict__ huge, BuildCtl* bc) {
+                             uint32_t* __restrict__ ucnt) {
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
          u += (long long)gridDim.x * blockDim.x) {
         const uint32_t o = off[u];
@@ -301,9 +487,21 @@ __global__ void k_sort_small(int n, const uint32_t* __restrict__ off, uint32_t* 
             ucnt[u] = thread_sort_row<16>(s, len);
         } else if (len <= kSmallMax) {
             ucnt[u] = thread_sort_row<32>(s, len);
-        } else if (len <= kMidMax) {
+        }  // longer rows: listed by k_classify, sorted by the class kernels
+    }
+}
+
+// Lists the rows longer than kSmallMax by size class (from the offsets alone,
+// so that the host can read the classes while the scatter runs).
+__global__ void k_classify(int n, const uint32_t* __restrict__ off, int* __restrict__ mid,
+                           int* __restrict__ big, int* __restrict__ huge, BuildCtl* bc) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x) {
+        const uint32_t len = off[u + 1] - off[u];
+        if (len <= (uint32_t)kSmallMax) continue;
+        if (len <= (uint32_t)kMidMax) {
             mid[atomicAdd(&bc->n_mid, 1u)] = (int)u;
-        } else if (len <= kBigMax) {
+        } else if (len <= (uint32_t)kBigMax) {
             big[atomicAdd(&bc->n_big, 1u)] = (int)u;
         } else {
             huge[atomicAdd(&bc->n_huge, 1u)] = (int)u;
@@ -490,90 +688,133 @@ __global__ void __launch_bounds__(kBigT) k_sort_big(const int* __restrict__ big,
     }
 }
 
-// ------------------------------------------------------------------ hub rows: global radix sort
-constexpr int kRsT = 512, kRsWarps = kRsT / 32, kRsKpt = 8, kRsTile = kRsT * kRsKpt;
+// ------------------------------------------------------------------ LSD radix sort of 64-bit keys
+// Tiles of kRsTile keys; one 8-bit digit per pass.  k_rs_hist counts each
+// tile's digits; one exclusive scan of the digit-major count matrix gives the
+// output start of every (digit, tile) run; k_rs_scatter ranks the tile's keys
+// by digit (stable: in input order), stages them in shared memory in digit
+// order and writes each digit's run contiguously.
+constexpr int kRsT = 256, kRsWarps = kRsT / 32, kRsKpt = 16, kRsTile = kRsT * kRsKpt;
 
 __global__ void __launch_bounds__(kRsT) k_rs_hist(const unsigned long long* __restrict__ keys,
                                                   long long N, int shift, uint32_t* hist,
                                                   long long nt) {
-    __shared__ uint32_t sh[256];
-    for (int d = threadIdx.x; d < 256; d += kRsT) sh[d] = 0;
+    __shared__ uint32_t sh[kRsWarps][256];  // one histogram per warp: fewer colliding adds
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; q++) sh[q][threadIdx.x] = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kRsTile;
+    unsigned long long k[kRsKpt];
 #pragma unroll
     for (int i = 0; i < kRsKpt; i++) {
         const long long idx = base + (long long)i * kRsT + threadIdx.x;
-        if (idx < N) atomicAdd(&sh[(keys[idx] >> shift) & 255u], 1u);
+        k[i] = idx < N ? keys[idx] : 0ull;
     }
+#pragma unroll
+    for (int i = 0; i < kRsKpt; i++)
+        if (base + (long long)i * kRsT + threadIdx.x < N) atomicAdd(&sh[w][(k[i] >> shift) & 255u], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += kRsT) hist[(long long)d * nt + blockIdx.x] = sh[d];
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; q++) c += sh[q][threadIdx.x];
+    hist[(long long)threadIdx.x * nt + blockIdx.x] = c;
 }
 
-// Stable scatter: within a tile, warp w owns keys [w*256, w*256+256) and walks
-// them in 8 rounds of 32; ranks follow (warp, round, lane) = input order.
-__global__ void __launch_bounds__(kRsT) k_rs_scatter(const unsigned long long* __restrict__ in,
-                                                     unsigned long long* __restrict__ out,
-                                                     long long N, int shift,
-                                                     const uint32_t* __restrict__ off,
-                                                     long long nt) {
+// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes in
+// `valid` (one ballot per digit bit).
+__device__ __forceinline__ unsigned digit_peers(unsigned d, unsigned valid) {
+    unsigned peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned m = __ballot_sync(kFull, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
+// Warp w owns keys [w*512, w*512 + 512) of the tile and walks them in 16
+// rounds of 32; ranks follow (warp, round, lane), which is input order.
+__global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(const unsigned long long* __restrict__ in,
+                                                        unsigned long long* __restrict__ out,
+                                                        long long N, int shift,
+                                                        const uint32_t* __restrict__ off,
+                                                        long long nt) {
+    __shared__ unsigned long long sk[kRsTile];
     __shared__ uint32_t wc[kRsWarps][256];
-    __shared__ uint32_t soff[256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
-    for (int d = threadIdx.x; d < 256; d += kRsT) soff[d] = off[(long long)d * nt + blockIdx.x];
-    __syncthreads();
+    __shared__ uint32_t dstart[256], goff[256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const long long base = (long long)blockIdx.x * kRsTile + (long long)w * (32 * kRsKpt);
+    const long long tile0 = (long long)blockIdx.x * kRsTile;
+    const long long base = tile0 + (long long)w * (32 * kRsKpt);
     unsigned long long key[kRsKpt];
     uint32_t rank[kRsKpt];
-    int dig[kRsKpt];
+    // the tile's keys and its run starts are fetched together, before any wait
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
         const long long idx = base + r * 32 + lane;
-        const bool valid = idx < N;
-        const unsigned long long k = valid ? in[idx] : 0ull;
-        const int d = valid ? (int)((k >> shift) & 255u) : 256 + lane;
-        const unsigned peers = __match_any_sync(kFull, d);
+        key[r] = idx < N ? in[idx] : 0ull;
+    }
+    const uint32_t my_goff = off[(long long)tid * nt + blockIdx.x];
+    for (int i = tid; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRsKpt; r++) {
+        const bool valid = base + r * 32 + lane < N;
+        const unsigned d = (unsigned)(key[r] >> shift) & 255u;
+        const unsigned peers = digit_peers(d, __ballot_sync(kFull, valid));
         const unsigned lower = peers & lt_mask;
-        uint32_t before = valid ? wc[w][d] : 0u;
+        const uint32_t before = valid ? wc[w][d] : 0u;
         __syncwarp();
         if (valid && lower == 0) wc[w][d] = before + (uint32_t)__popc(peers);
         __syncwarp();
-        key[r] = k;
         rank[r] = before + (uint32_t)__popc(lower);
-        dig[r] = valid ? d : -1;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += kRsT) {
-        uint32_t run = 0;
+    // thread tid = digit: exclusive prefix over the warps, then over the digits
+    uint32_t run = 0;
 #pragma unroll
-        for (int ww = 0; ww < kRsWarps; ww++) {
-            const uint32_t c = wc[ww][d];
-            wc[ww][d] = run;
-            run += c;
+    for (int ww = 0; ww < kRsWarps; ww++) {
+        const uint32_t c = wc[ww][tid];
+        wc[ww][tid] = run;
+        run += c;
+    }
+    unsigned long long tot;
+    dstart[tid] = (uint32_t)block_excl_scan(run, &tot);
+    goff[tid] = my_goff;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRsKpt; r++) {
+        if (base + r * 32 + lane < N) {
+            const unsigned d = (unsigned)(key[r] >> shift) & 255u;
+            sk[dstart[d] + wc[w][d] + rank[r]] = key[r];
         }
     }
     __syncthreads();
+    const int cnt = (int)min((long long)kRsTile, N - tile0);
 #pragma unroll
-    for (int r = 0; r < kRsKpt; r++)
-        if (dig[r] >= 0) out[(long long)soff[dig[r]] + wc[w][dig[r]] + rank[r]] = key[r];
+    for (int r = 0; r < kRsKpt; r++) {
+        const int p = r * kRsT + tid;
+        if (p < cnt) {
+            const unsigned long long k = sk[p];
+            const unsigned d = (unsigned)(k >> shift) & 255u;
+            out[(long long)goff[d] + (uint32_t)(p - (int)dstart[d])] = k;
+        }
+    }
 }
 
 // Sorts keys[0..N) by bits [0, lowbits) then [32, 32 + highbits) (LSD); returns
 // the buffer holding the result.
 cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long long N, int lowbits,
-                       int highbits, cudaStream_t st, unsigned long long** result) {
+                       int highbits, cudaStream_t st, unsigned long long** result, Temp* tmp) {
     *result = keys;
     if (N <= 1) return cudaSuccess;
     const long long nt = (N + kRsTile - 1) / kRsTile;
     uint32_t *hist = nullptr, *off = nullptr;
-    cudaError_t e = pool_alloc((void**)&hist, sizeof(uint32_t) * 256 * nt, st);
+    cudaError_t e = tmp->get(&hist, (size_t)256 * nt);
+    if (e == cudaSuccess) e = tmp->get(&off, (size_t)256 * nt);
     if (e != cudaSuccess) return e;
-    e = pool_alloc((void**)&off, sizeof(uint32_t) * 256 * nt, st);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(hist, st);
-        return e;
-    }
     std::vector<int> shifts;
     for (int s = 0; s < lowbits; s += 8) shifts.push_back(s);
     for (int s = 0; s < highbits; s += 8) shifts.push_back(32 + s);
@@ -583,7 +824,7 @@ cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long l
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st);
+        e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st, tmp);
         if (e != cudaSuccess) break;
         k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(a, b, N, sh, off, nt);
         count_launch();
@@ -591,8 +832,6 @@ cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long l
         if (e != cudaSuccess) break;
         std::swap(a, b);
     }
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(off, st);
     *result = a;
     return e;
 }
@@ -755,26 +994,87 @@ __global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int
         out->nnz = off_bytes == 8 ? ((const long long*)row_ptr)[n] : (long long)((const int*)row_ptr)[n];
 }
 
+// ------------------------------------------------------------------ sorted build
+// For graphs with many entries per vertex: both directed entries of every
+// sample as a 64-bit key (row << 32 | column), one LSD radix sort over the row
+// and column bits, then repeats dropped while col_idx and the row counts are
+// written.  No per-row atomics on hot rows and no per-row sorts.
+constexpr unsigned long long kNoKey = ~0ull;  // a dropped sample: sorts last
+
+__global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst, long long S,
+                          int n, ulonglong2* __restrict__ keys, BuildCtl* bc) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int s = src[i], d = dst[i];
+        ulonglong2 k = make_ulonglong2(kNoKey, kNoKey);
+        if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n) {
+            bc->bad = 1;
+        } else if (s != d) {
+            k.x = ((unsigned long long)(unsigned)s << 32) | (unsigned)d;
+            k.y = ((unsigned long long)(unsigned)d << 32) | (unsigned)s;
+        }
+        keys[i] = k;
+    }
+}
+
+__device__ __forceinline__ bool sb_first(const unsigned long long* keys, long long i) {
+    const unsigned long long k = keys[i];
+    return k != kNoKey && (i == 0 || keys[i - 1] != k);
+}
+
+// Distinct keys per tile of kRsTile sorted keys.
+__global__ void __launch_bounds__(kRsT) k_sb_count(const unsigned long long* __restrict__ keys,
+                                                   long long N, uint32_t* __restrict__ tsum) {
+    const long long base = (long long)blockIdx.x * kRsTile;
+    unsigned c = 0;
+#pragma unroll 4
+    for (int i = 0; i < kRsKpt; i++) {
+        const long long idx = base + (long long)i * kRsT + threadIdx.x;
+        if (idx < N && sb_first(keys, idx)) c++;
+    }
+    unsigned long long tot;
+    block_excl_scan(c, &tot);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = (uint32_t)tot;
+}
+
+// col_idx[position among distinct keys] = column; ucnt[row] += distinct keys
+// (sorted keys: a warp's lanes share one or two rows, one add per row).
+__global__ void __launch_bounds__(kRsT) k_sb_emit(const unsigned long long* __restrict__ keys,
+                                                  long long N, const uint32_t* __restrict__ toff,
+                                                  int* __restrict__ col,
+                                                  uint32_t* __restrict__ ucnt) {
+    __shared__ uint32_t wsum[kRsWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kRsTile;
+    uint32_t run = toff[blockIdx.x];
+    for (int i = 0; i < kRsKpt; i++) {
+        const long long idx = base + (long long)i * kRsT + threadIdx.x;
+        const bool f = idx < N && sb_first(keys, idx);
+        const unsigned m = __ballot_sync(kFull, f);
+        if (lane == 0) wsum[w] = (uint32_t)__popc(m);
+        __syncthreads();
+        uint32_t before = 0, all = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRsWarps; ww++) {
+            const uint32_t c = wsum[ww];
+            before += ww < w ? c : 0u;
+            all += c;
+        }
+        __syncthreads();
+        const unsigned long long k = f ? keys[idx] : 0ull;
+        const unsigned row = (unsigned)(k >> 32);
+        if (f) col[run + before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (int)(unsigned)k;
+        const unsigned peers = __match_any_sync(kFull, f ? row : 0xffffffffu);
+        if (f && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&ucnt[row], (uint32_t)__popc(peers));
+        run += all;
+    }
+}
+
 int id_bits(long long n) {
     int b = 0;
     while ((1ll << b) < n) b++;
     return b;
 }
-
-struct Temp {
-    cudaStream_t st;
-    std::vector<void*> ptrs;
-    explicit Temp(cudaStream_t s) : st(s) {}
-    ~Temp() {
-        for (void* p : ptrs) cudaFreeAsync(p, st);
-    }
-    template <typename T>
-    cudaError_t get(T** p, size_t count) {
-        cudaError_t e = pool_alloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
-        if (e == cudaSuccess) ptrs.push_back(*p);
-        return e;
-    }
-};
 
 kcore_status cuda_fail(cudaError_t e, const char* what, std::string* err) {
     cudaGetLastError();
@@ -808,31 +1108,63 @@ cudaError_t compact(int64_t n, const uint32_t* off, const uint32_t* seg, const u
     return cudaGetLastError();
 }
 
+// A pinned copy of the build state and the event that marks its arrival;
+// released only once the copy has landed.
+struct ClassRead {
+    BuildCtl* h = nullptr;
+    cudaEvent_t ev = nullptr;
+    ~ClassRead() {
+        if (ev) {
+            cudaEventSynchronize(ev);
+            cudaEventDestroy(ev);
+        }
+        if (h) pinned_put(h);
+    }
+};
+
 // Steps 2-5, after the counts are in cnt.  `scatter` launches step 3.
 template <typename ScatterFn>
 kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* bc, int off_bytes,
                     cudaStream_t st, DevCsr* out, std::string* err, ScatterFn scatter) {
     // N: an upper bound of the entries (two per input sample or entry)
     const long long nn = std::max<int64_t>(n, 1);
+    const size_t nbig = (size_t)std::min<long long>(nn, N / (kMidMax + 1) + 1);
+    const size_t nhuge = (size_t)std::min<long long>(nn, N / (kBigMax + 1) + 1);
     uint32_t *off = nullptr, *seg = nullptr, *ucnt = nullptr;
     int *mid = nullptr, *big = nullptr, *huge = nullptr;
+    KC_TRY(tmp.reserve(Temp::round(4 * (nn + 1)) + Temp::round(4 * (size_t)std::max<long long>(N, 1)) +
+                       2 * Temp::round(4 * nn) + Temp::round(4 * nbig) + Temp::round(4 * nhuge) +
+                       2 * scan_scratch_bytes(n)),
+           "temporaries");
     KC_TRY(tmp.get(&off, (size_t)nn + 1), "row offsets");
-    KC_TRY(exclusive_scan(ReadU32{cnt}, n, off, true, st), "offset scan");
+    KC_TRY(exclusive_scan(ReadU32{cnt}, n, off, true, st, &tmp), "offset scan");
     BuildCtl hbc;
     KC_TRY(tmp.get(&seg, (size_t)N), "segments");
     KC_TRY(tmp.get(&ucnt, (size_t)nn), "distinct counts");
     KC_TRY(tmp.get(&mid, (size_t)nn), "row lists");
-    KC_TRY(tmp.get(&big, (size_t)std::min<long long>(nn, N / (kMidMax + 1) + 1)), "row lists");
-    KC_TRY(tmp.get(&huge, (size_t)std::min<long long>(nn, N / (kBigMax + 1) + 1)), "row lists");
+    KC_TRY(tmp.get(&big, nbig), "row lists");
+    KC_TRY(tmp.get(&huge, nhuge), "row lists");
+    // the size classes, copied to the host while the scatter and the small
+    // sorts run: the host waits on the copy, not on the stream
+    if (n > 0) {
+        k_classify<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, mid, big, huge, bc);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "classify rows");
+    }
+    ClassRead cr;
+    KC_TRY(pinned_get((void**)&cr.h, sizeof(BuildCtl)), "pinned buffer");
+    KC_TRY(cudaEventCreateWithFlags(&cr.ev, cudaEventDisableTiming), "event");
+    KC_TRY(cudaMemcpyAsync(cr.h, bc, sizeof(BuildCtl), cudaMemcpyDeviceToHost, st), "read classes");
+    KC_TRY(cudaEventRecord(cr.ev, st), "event");
     KC_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nn, st), "memset");  // cnt becomes the fill counter
     KC_TRY(scatter(off, cnt, seg), "scatter");
     if (n > 0) {
-        k_sort_small<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, seg, ucnt, mid, big, huge, bc);
+        k_sort_small<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, seg, ucnt);
         count_launch();
         KC_TRY(cudaGetLastError(), "sort small rows");
     }
-    KC_TRY(cudaMemcpyAsync(&hbc, bc, sizeof(BuildCtl), cudaMemcpyDeviceToHost, st), "read classes");
-    KC_TRY(cudaStreamSynchronize(st), "sync");
+    KC_TRY(cudaEventSynchronize(cr.ev), "sync");
+    hbc = *cr.h;
     if (hbc.bad) {
         *err = "an edge endpoint or a row offset is out of range";
         return KCORE_ERR_INVALID;
@@ -859,12 +1191,12 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
         KC_TRY(tmp.get(&keys, (size_t)H), "hub keys");
         KC_TRY(tmp.get(&alt, (size_t)H), "hub keys");
         KC_TRY(tmp.get(&hoff, (size_t)hbc.n_huge + 1), "hub offsets");
-        KC_TRY(exclusive_scan(HubLen{huge, off}, (long long)hbc.n_huge, hoff, true, st), "hub offsets");
+        KC_TRY(exclusive_scan(HubLen{huge, off}, (long long)hbc.n_huge, hoff, true, st, &tmp), "hub offsets");
         const unsigned g = std::min<unsigned>(hbc.n_huge, 152u * 4u);
         k_huge_keys<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, seg, keys);
         count_launch();
         KC_TRY(cudaGetLastError(), "hub keys");
-        KC_TRY(radix_sort(keys, alt, H, id_bits(n), id_bits(hbc.n_huge), st, &sorted), "hub sort");
+        KC_TRY(radix_sort(keys, alt, H, id_bits(n), id_bits(hbc.n_huge), st, &sorted, &tmp), "hub sort");
         k_huge_back<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, sorted, seg, ucnt);
         count_launch();
         KC_TRY(cudaGetLastError(), "hub write back");
@@ -875,9 +1207,9 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
     s = dmalloc((void**)&out->col, sizeof(int) * std::max<size_t>(N, 1), err, st);
     if (s != KCORE_OK) return s;
     if (off_bytes == 8)
-        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (long long*)out->row_ptr, true, st), "row scan");
+        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (long long*)out->row_ptr, true, st, &tmp), "row scan");
     else
-        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (int*)out->row_ptr, true, st), "row scan");
+        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (int*)out->row_ptr, true, st, &tmp), "row scan");
     if (n > 0) {
         const int* const lists[3] = {mid, big, huge};
         const unsigned* const counts[3] = {&bc->n_mid, &bc->n_big, &bc->n_huge};
@@ -895,6 +1227,58 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
     return KCORE_OK;
 }
 
+// The sorted build (kernels above); the host waits once, at the end, for the
+// range flag.
+kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, const int* dst,
+                          BuildCtl* bc, int off_bytes, cudaStream_t st, DevCsr* out,
+                          std::string* err) {
+    const long long N = 2 * S, nn = std::max<int64_t>(n, 1);
+    const long long nt = (N + kRsTile - 1) / kRsTile;
+    unsigned long long *keys = nullptr, *alt = nullptr, *sorted = nullptr;
+    uint32_t *ucnt = nullptr, *tsum = nullptr, *toff = nullptr;
+    KC_TRY(tmp.reserve(2 * Temp::round(8 * (size_t)N) + Temp::round(4 * nn) + 2 * Temp::round(4 * (nt + 1)) +
+                       2 * Temp::round(4 * 256 * (size_t)nt) + scan_scratch_bytes(256 * nt) +
+                       scan_scratch_bytes(nt) + scan_scratch_bytes(n)),
+           "temporaries");
+    KC_TRY(tmp.get(&keys, (size_t)N), "keys");
+    KC_TRY(tmp.get(&alt, (size_t)N), "keys");
+    KC_TRY(tmp.get(&ucnt, (size_t)nn), "distinct counts");
+    KC_TRY(tmp.get(&tsum, (size_t)nt), "tile counts");
+    KC_TRY(tmp.get(&toff, (size_t)nt + 1), "tile offsets");
+    KC_TRY(cudaMemsetAsync(ucnt, 0, sizeof(uint32_t) * nn, st), "memset");
+    k_sb_keys<<<grid_for(S, 256), 256, 0, st>>>(src, dst, S, (int)n, (ulonglong2*)keys, bc);
+    count_launch();
+    KC_TRY(cudaGetLastError(), "keys");
+    const int bits = id_bits(n);
+    KC_TRY(radix_sort(keys, alt, N, bits, bits, st, &sorted, &tmp), "sort");
+    k_sb_count<<<(unsigned)nt, kRsT, 0, st>>>(sorted, N, tsum);
+    count_launch();
+    KC_TRY(cudaGetLastError(), "distinct count");
+    KC_TRY(exclusive_scan(ReadU32{tsum}, nt, toff, true, st, &tmp), "tile scan");
+    kcore_status s = dmalloc(&out->row_ptr, (size_t)off_bytes * (n + 1), err, st);
+    if (s != KCORE_OK) return s;
+    s = dmalloc((void**)&out->col, sizeof(int) * std::max<size_t>(N, 1), err, st);
+    if (s != KCORE_OK) return s;
+    k_sb_emit<<<(unsigned)nt, kRsT, 0, st>>>(sorted, N, toff, out->col, ucnt);
+    count_launch();
+    KC_TRY(cudaGetLastError(), "emit");
+    if (off_bytes == 8)
+        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (long long*)out->row_ptr, true, st, &tmp), "row scan");
+    else
+        KC_TRY(exclusive_scan(ReadU32{ucnt}, n, (int*)out->row_ptr, true, st, &tmp), "row scan");
+    int hbad = 0;
+    KC_TRY(cudaMemcpyAsync(&hbad, &bc->bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+    KC_TRY(cudaStreamSynchronize(st), "sync");
+    if (hbad) {
+        *err = "an edge endpoint or a row offset is out of range";
+        return KCORE_ERR_INVALID;
+    }
+    out->n = n;
+    out->nnz = -1;  // row_ptr[n], read by the caller's next wait
+    out->off_bytes = off_bytes;
+    return KCORE_OK;
+}
+
 }  // namespace
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,
@@ -903,7 +1287,8 @@ cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long lo
 }
 
 kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const int* dst,
-                            int off_bytes, cudaStream_t st, DevCsr* out, std::string* err) {
+                            int off_bytes, int sort_mode, cudaStream_t st, DevCsr* out,
+                            std::string* err) {
     if (samples > 0x7fffffffLL) {
         *err = "at most 2^31-1 samples per graph";
         return KCORE_ERR_INVALID;
@@ -911,12 +1296,39 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
     Temp tmp(st);
     uint32_t* cnt = nullptr;
     BuildCtl* bc = nullptr;
-    KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
+    const size_t cnt_bytes = sizeof(uint32_t) * std::max<int64_t>(n, 1);
+    KC_TRY(tmp.reserve(Temp::round(sizeof(BuildCtl)) + Temp::round(cnt_bytes)), "temporaries");
     KC_TRY(tmp.get(&bc, 1), "build state");
-    KC_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), st), "memset");
-    KC_TRY(cudaMemsetAsync(bc, 0, sizeof(BuildCtl), st), "memset");
+    KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
+    KC_TRY(cudaMemsetAsync(tmp.base, 0, tmp.used, st), "memset");  // the state and the counts
+    if (samples > 0 && sort_mode > 0)
+        return sorted_build(tmp, n, samples, src, dst, bc, off_bytes, st, out, err);
+    // Automatic choice, for large inputs of average degree >= kSortAutoDegree
+    // only (the others skip the wait): the sorted build when rows of more than
+    // kSmallMax entries hold at least half of the entries, estimated from every
+    // kSortProbe-th sample.  Per-row counting and sorting is cheaper while rows
+    // are short; hub rows make its atomics collide and need the larger sorts.
+    // Either way the cleaned graph is the same.
+    if (sort_mode == 0 && samples >= kSortAutoSamples && 2 * samples >= kSortAutoDegree * n) {
+        k_count_coo<<<grid_for(samples / kSortProbe + 1, 256), 256, 0, st>>>(src, dst, samples, (int)n,
+                                                                           cnt, bc, kSortProbe);
+        count_launch();
+        k_heavy<<<grid_for(n, 256), 256, 0, st>>>(cnt, n, kSmallMax / kSortProbe, bc);
+        count_launch();
+        KC_TRY(cudaGetLastError(), "row classes");
+        BuildCtl hbc;
+        KC_TRY(cudaMemcpyAsync(&hbc, bc, sizeof(BuildCtl), cudaMemcpyDeviceToHost, st), "read");
+        KC_TRY(cudaStreamSynchronize(st), "sync");
+        if (hbc.bad) {
+            *err = "an edge endpoint or a row offset is out of range";
+            return KCORE_ERR_INVALID;
+        }
+        if (hbc.entries > 0 && 2 * hbc.heavy >= hbc.entries)
+            return sorted_build(tmp, n, samples, src, dst, bc, off_bytes, st, out, err);
+        KC_TRY(cudaMemsetAsync(cnt, 0, cnt_bytes, st), "memset");
+    }
     if (samples > 0) {
-        k_count_coo<<<grid_for(samples, 256), 256, 0, st>>>(src, dst, samples, (int)n, cnt, bc);
+        k_count_coo<<<grid_for(samples, 256), 256, 0, st>>>(src, dst, samples, (int)n, cnt, bc, 1);
         count_launch();
         KC_TRY(cudaGetLastError(), "count");
     }
@@ -941,10 +1353,11 @@ kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, co
     Temp tmp(st);
     uint32_t* cnt = nullptr;
     BuildCtl* bc = nullptr;
-    KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
+    const size_t cnt_bytes = sizeof(uint32_t) * std::max<int64_t>(n, 1);
+    KC_TRY(tmp.reserve(Temp::round(sizeof(BuildCtl)) + Temp::round(cnt_bytes)), "temporaries");
     KC_TRY(tmp.get(&bc, 1), "build state");
-    KC_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), st), "memset");
-    KC_TRY(cudaMemsetAsync(bc, 0, sizeof(BuildCtl), st), "memset");
+    KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
+    KC_TRY(cudaMemsetAsync(tmp.base, 0, tmp.used, st), "memset");  // the state and the counts
     const int g = grid_for(n * 32, 256);
     if (n > 0) {
         if (in_off_bytes == 8)
@@ -1002,6 +1415,9 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
     Temp tmp(st);
     const int nb = (int)((n + kTsT - 1) / kTsT);
     uint32_t *cnt = nullptr, *off = nullptr;
+    KC_TRY(tmp.reserve(Temp::round(4 * (size_t)kTiers * nb) + Temp::round(4 * ((size_t)kTiers * nb + 1)) +
+                       scan_scratch_bytes((long long)kTiers * nb)),
+           "temporaries");
     KC_TRY(tmp.get(&cnt, (size_t)kTiers * nb), "tier counts");
     KC_TRY(tmp.get(&off, (size_t)kTiers * nb + 1), "tier offsets");
     if (off_bytes == 8)
@@ -1011,7 +1427,7 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
         k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, &dout->bad);
     count_launch();
     KC_TRY(cudaGetLastError(), "tier count");
-    KC_TRY(exclusive_scan(ReadU32{cnt}, (long long)kTiers * nb, off, true, st), "tier scan");
+    KC_TRY(exclusive_scan(ReadU32{cnt}, (long long)kTiers * nb, off, true, st, &tmp), "tier scan");
     if (off_bytes == 8)
         k_tier_write<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, off, nb,
                                           est0, init_list);

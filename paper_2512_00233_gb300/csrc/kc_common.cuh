@@ -109,10 +109,13 @@ struct DevCsr {
     int* col = nullptr;
 };
 
-// Raw samples (device) -> clean CSR (device, allocated here).  Returns a
+// Raw samples (device) -> clean CSR (device, allocated here).  sort_mode 1:
+// the sorted build (one radix sort of all entries); -1: rows counted,
+// scattered and sorted one by one; 0: chosen from the row sizes.  Returns a
 // kcore_status; on error *err names the problem.
 kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const int* dst,
-                            int off_bytes, cudaStream_t st, DevCsr* out, std::string* err);
+                            int off_bytes, int sort_mode, cudaStream_t st, DevCsr* out,
+                            std::string* err);
 kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, const int* col,
                             int64_t nnz, int off_bytes, cudaStream_t st, DevCsr* out,
                             std::string* err);

@@ -46,6 +46,7 @@ def test_defaults_and_version():
     assert o.struct_size == ctypes.sizeof(K.Options)
     assert (o.t_lo, o.t_hi, o.block) == (16, 2048, 512)
     assert o.timeout_s > 0
+    assert o.build_sort == 0
     assert "sm_103a" in K.version()
     s = K.default_serve_options()
     assert s.struct_size == ctypes.sizeof(K.ServeOptions)

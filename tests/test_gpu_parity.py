@@ -198,6 +198,65 @@ def test_csr_input_paths(torch_cuda):
         np.testing.assert_array_equal(g.run().cpu().numpy(), core)
 
 
+# ------------------------------------------------------------------ the two COO cleaners
+SORTED, COUNTED = 1, -1   # build_sort: the sorted build / rows counted one by one
+
+
+def cleaner_cases():
+    rng = np.random.default_rng(77)
+    cases = []
+    # n a power of two (the largest id has every id bit set), hubs in every
+    # row size class up to the hub radix path (> 16384 entries)
+    src, dst = random_graph(rng, 1 << 12, 6 << 12, hubs=4, hub_deg=9000)
+    src = np.concatenate([src, np.full(20000, 5, np.int32)])
+    dst = np.concatenate([dst, rng.integers(0, 1 << 12, 20000).astype(np.int32)])
+    cases.append(("pow2_hubs", 1 << 12, src, dst))
+    # n just above a power of two, loops and repeats, isolated vertices at both ends
+    n = (1 << 11) + 3
+    a = rng.integers(100, n - 100, 4 * n).astype(np.int32)
+    b = rng.integers(100, n - 100, 4 * n).astype(np.int32)
+    a = np.concatenate([a, a[:500], np.arange(100, 400, dtype=np.int32)])
+    b = np.concatenate([b, b[:500], np.arange(100, 400, dtype=np.int32)])
+    cases.append(("loops_repeats", n, a, b))
+    cases.append(("one_edge", 2, np.array([1, 1, 0], np.int32), np.array([0, 1, 1], np.int32)))
+    cases.append(("only_loops", 4, np.arange(4, dtype=np.int32), np.arange(4, dtype=np.int32)))
+    cases.append(("single_vertex", 1, np.zeros(3, np.int32), np.zeros(3, np.int32)))
+    g = graphgen.rmat(1 << 13, 16 << 13, 0.57, 0.19, 0.19, seed=4)
+    cases.append(("rmat13", g.n, g.src, g.dst))
+    return cases
+
+
+@pytest.mark.parametrize("case", cleaner_cases(), ids=lambda c: c[0])
+@pytest.mark.parametrize("rp_bytes", [4, 8])
+def test_coo_cleaners_match_oracle(torch_cuda, case, rp_bytes):
+    """Both COO cleaners (one radix sort of all entries; per-row counting and
+    sorting) give the oracle's CSR entry for entry, and the same coreness."""
+    _, n, src, dst = case
+    rp, col, core = oracle_of(n, src, dst)
+    for mode in (SORTED, COUNTED, 0):
+        opts = K.default_options(build_sort=mode) if mode else None
+        with K.Graph.from_coo(n, src, dst, rp_bytes, options=opts) as g:
+            grp, gcol = g.csr()
+            np.testing.assert_array_equal(grp, rp, err_msg=str(mode))
+            np.testing.assert_array_equal(gcol, col, err_msg=str(mode))
+            np.testing.assert_array_equal(g.run().cpu().numpy(), core, err_msg=str(mode))
+    t = torch_cuda   # device samples through the sorted build
+    with K.Graph.from_coo(n, t.from_numpy(np.asarray(src)).cuda(), t.from_numpy(np.asarray(dst)).cuda(),
+                          rp_bytes, options=K.default_options(build_sort=SORTED)) as g:
+        grp, gcol = g.csr()
+        np.testing.assert_array_equal(grp, rp)
+        np.testing.assert_array_equal(gcol, col)
+
+
+@pytest.mark.parametrize("mode", [SORTED, COUNTED])
+def test_coo_cleaners_reject_bad_ids(torch_cuda, mode):
+    opts = K.default_options(build_sort=mode)
+    for s, d in (([0, 5, 1], [1, 1, 2]), ([0, -1, 1], [1, 1, 2])):
+        with pytest.raises(K.KCoreError) as e:
+            K.Graph.from_coo(5, np.array(s, np.int32), np.array(d, np.int32), options=opts)
+        assert e.value.status == K.KCORE_ERR_INVALID
+
+
 def test_invalid_inputs_are_rejected(torch_cuda):
     with pytest.raises(K.KCoreError) as e:
         K.Graph.from_coo(5, np.array([0, 5], np.int32), np.array([1, 1], np.int32))
