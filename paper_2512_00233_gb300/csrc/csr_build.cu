@@ -319,11 +319,13 @@ struct BuildCtl {
     unsigned long long entries, heavy;  // all counted entries; those in rows above kSmallMax
 };
 
-// Every step-th sample (step 1: all of them).
+// The samples of every step-th run of 256 (step 1: all of them); runs keep
+// the reads coalesced when only a share of the samples is counted.
 __global__ void k_count_coo(const int* __restrict__ src, const int* __restrict__ dst, long long S,
                             int n, uint32_t* __restrict__ cnt, BuildCtl* bc, int step) {
-    for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * step; i < S;
-         i += (long long)gridDim.x * blockDim.x * step) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;; j += (long long)gridDim.x * blockDim.x) {
+        const long long i = ((j >> 8) * step << 8) | (j & 255);
+        if (i >= S) break;
         const int s = src[i], d = dst[i];
         if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n) {
             bc->bad = 1;
@@ -335,8 +337,10 @@ __global__ void k_count_coo(const int* __restrict__ src, const int* __restrict__
     }
 }
 
-// Entries in rows of more than `limit` entries, and all entries.
+// Entries in rows of more than `limit` entries, and all entries (one pair of
+// atomics per block).
 __global__ void k_heavy(const uint32_t* __restrict__ cnt, long long n, uint32_t limit, BuildCtl* bc) {
+    __shared__ unsigned long long ws[2][32];
     unsigned long long all = 0, heavy = 0;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
          u += (long long)gridDim.x * blockDim.x) {
@@ -349,9 +353,21 @@ __global__ void k_heavy(const uint32_t* __restrict__ cnt, long long n, uint32_t 
         all += __shfl_down_sync(kFull, all, o);
         heavy += __shfl_down_sync(kFull, heavy, o);
     }
-    if ((threadIdx.x & 31) == 0 && all) {
-        atomicAdd(&bc->entries, all);
-        atomicAdd(&bc->heavy, heavy);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        ws[0][w] = all;
+        ws[1][w] = heavy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+            all += ws[0][q];
+            heavy += ws[1][q];
+        }
+        if (all) {
+            atomicAdd(&bc->entries, all);
+            atomicAdd(&bc->heavy, heavy);
+        }
     }
 }
 
@@ -695,10 +711,18 @@ __global__ void __launch_bounds__(kBigT) k_sort_big(const int* __restrict__ big,
 // by digit (stable: in input order), stages them in shared memory in digit
 // order and writes each digit's run contiguously.
 constexpr int kRsT = 256, kRsWarps = kRsT / 32, kRsKpt = 16, kRsTile = kRsT * kRsKpt;
+constexpr unsigned long long kNoKey = ~0ull;  // a dropped entry: sorts last
 
-__global__ void __launch_bounds__(kRsT) k_rs_hist(const unsigned long long* __restrict__ keys,
-                                                  long long N, int shift, uint32_t* hist,
-                                                  long long nt) {
+// The keys a pass reads: the previous pass's buffer.
+struct KeyIn {
+    const unsigned long long* k;
+    __device__ __forceinline__ unsigned long long operator()(long long j) const { return k[j]; }
+    __device__ __forceinline__ bool invalid(long long) const { return false; }
+};
+
+template <typename In>
+__global__ void __launch_bounds__(kRsT) k_rs_hist(In keys, long long N, int shift, uint32_t* hist,
+                                                  long long nt, int* bad) {
     __shared__ uint32_t sh[kRsWarps][256];  // one histogram per warp: fewer colliding adds
     const int w = threadIdx.x >> 5;
 #pragma unroll
@@ -709,7 +733,8 @@ __global__ void __launch_bounds__(kRsT) k_rs_hist(const unsigned long long* __re
 #pragma unroll
     for (int i = 0; i < kRsKpt; i++) {
         const long long idx = base + (long long)i * kRsT + threadIdx.x;
-        k[i] = idx < N ? keys[idx] : 0ull;
+        k[i] = idx < N ? keys(idx) : 0ull;
+        if (bad && idx < N && keys.invalid(idx)) *bad = 1;
     }
 #pragma unroll
     for (int i = 0; i < kRsKpt; i++)
@@ -736,8 +761,8 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d, unsigned valid) {
 
 // Warp w owns keys [w*512, w*512 + 512) of the tile and walks them in 16
 // rounds of 32; ranks follow (warp, round, lane), which is input order.
-__global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(const unsigned long long* __restrict__ in,
-                                                        unsigned long long* __restrict__ out,
+template <typename In>
+__global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(In in, unsigned long long* __restrict__ out,
                                                         long long N, int shift,
                                                         const uint32_t* __restrict__ off,
                                                         long long nt) {
@@ -754,7 +779,7 @@ __global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(const unsigned long long
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
         const long long idx = base + r * 32 + lane;
-        key[r] = idx < N ? in[idx] : 0ull;
+        key[r] = idx < N ? in(idx) : 0ull;
     }
     const uint32_t my_goff = off[(long long)tid * nt + blockIdx.x];
     for (int i = tid; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
@@ -804,12 +829,14 @@ __global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(const unsigned long long
     }
 }
 
-// Sorts keys[0..N) by bits [0, lowbits) then [32, 32 + highbits) (LSD); returns
-// the buffer holding the result.
-cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long long N, int lowbits,
-                       int highbits, cudaStream_t st, unsigned long long** result, Temp* tmp) {
-    *result = keys;
-    if (N <= 1) return cudaSuccess;
+// Sorts the N keys of `first` by bits [0, lowbits) then [32, 32 + highbits)
+// (LSD).  Pass p writes buf[p % 2] and the next pass reads it; *result is the
+// buffer holding the sorted keys.  `bad` (may be null) is raised when `first`
+// reports an invalid key.  N >= 1.
+template <typename In>
+cudaError_t radix_sort(In first, long long N, unsigned long long* buf0, unsigned long long* buf1,
+                       int lowbits, int highbits, cudaStream_t st, unsigned long long** result,
+                       Temp* tmp, int* bad) {
     const long long nt = (N + kRsTile - 1) / kRsTile;
     uint32_t *hist = nullptr, *off = nullptr;
     cudaError_t e = tmp->get(&hist, (size_t)256 * nt);
@@ -818,21 +845,29 @@ cudaError_t radix_sort(unsigned long long* keys, unsigned long long* alt, long l
     std::vector<int> shifts;
     for (int s = 0; s < lowbits; s += 8) shifts.push_back(s);
     for (int s = 0; s < highbits; s += 8) shifts.push_back(32 + s);
-    unsigned long long *a = keys, *b = alt;
-    for (int sh : shifts) {
-        k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(a, N, sh, hist, nt);
+    if (shifts.empty()) shifts.push_back(0);  // the keys still pass through once
+    unsigned long long* buf[2] = {buf0, buf1};
+    for (size_t p = 0; p < shifts.size() && e == cudaSuccess; p++) {
+        const int sh = shifts[p];
+        unsigned long long* out = buf[p % 2];
+        if (p == 0) {
+            k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(first, N, sh, hist, nt, bad);
+        } else {
+            k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(KeyIn{buf[(p - 1) % 2]}, N, sh, hist, nt,
+                                                     (int*)nullptr);
+        }
         count_launch();
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st, tmp);
         if (e != cudaSuccess) break;
-        e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st, tmp);
-        if (e != cudaSuccess) break;
-        k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(a, b, N, sh, off, nt);
+        if (p == 0)
+            k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(first, out, N, sh, off, nt);
+        else
+            k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(KeyIn{buf[(p - 1) % 2]}, out, N, sh, off, nt);
         count_launch();
         e = cudaGetLastError();
-        if (e != cudaSuccess) break;
-        std::swap(a, b);
+        *result = out;
     }
-    *result = a;
     return e;
 }
 
@@ -995,12 +1030,11 @@ __global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int
 }
 
 // ------------------------------------------------------------------ sorted build
-// For graphs with many entries per vertex: both directed entries of every
+// For graphs whose hub rows hold most entries: both directed entries of every
 // sample as a 64-bit key (row << 32 | column), one LSD radix sort over the row
 // and column bits, then repeats dropped while col_idx and the row counts are
-// written.  No per-row atomics on hot rows and no per-row sorts.
-constexpr unsigned long long kNoKey = ~0ull;  // a dropped sample: sorts last
-
+// written.  No per-row atomics on hot rows and no per-row sorts.  (Making the
+// keys inside the first radix pass instead was slower.)
 __global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst, long long S,
                           int n, ulonglong2* __restrict__ keys, BuildCtl* bc) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
@@ -1196,7 +1230,9 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
         k_huge_keys<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, seg, keys);
         count_launch();
         KC_TRY(cudaGetLastError(), "hub keys");
-        KC_TRY(radix_sort(keys, alt, H, id_bits(n), id_bits(hbc.n_huge), st, &sorted, &tmp), "hub sort");
+        KC_TRY(radix_sort(KeyIn{keys}, H, alt, keys, id_bits(n), id_bits(hbc.n_huge), st, &sorted, &tmp,
+                          (int*)nullptr),
+               "hub sort");
         k_huge_back<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, sorted, seg, ucnt);
         count_launch();
         KC_TRY(cudaGetLastError(), "hub write back");
@@ -1250,7 +1286,7 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     count_launch();
     KC_TRY(cudaGetLastError(), "keys");
     const int bits = id_bits(n);
-    KC_TRY(radix_sort(keys, alt, N, bits, bits, st, &sorted, &tmp), "sort");
+    KC_TRY(radix_sort(KeyIn{keys}, N, alt, keys, bits, bits, st, &sorted, &tmp, (int*)nullptr), "sort");
     k_sb_count<<<(unsigned)nt, kRsT, 0, st>>>(sorted, N, tsum);
     count_launch();
     KC_TRY(cudaGetLastError(), "distinct count");
@@ -1310,10 +1346,11 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
     // are short; hub rows make its atomics collide and need the larger sorts.
     // Either way the cleaned graph is the same.
     if (sort_mode == 0 && samples >= kSortAutoSamples && 2 * samples >= kSortAutoDegree * n) {
-        k_count_coo<<<grid_for(samples / kSortProbe + 1, 256), 256, 0, st>>>(src, dst, samples, (int)n,
-                                                                           cnt, bc, kSortProbe);
+        k_count_coo<<<grid_for(samples / kSortProbe + 256, 256), 256, 0, st>>>(src, dst, samples, (int)n,
+                                                                             cnt, bc, kSortProbe);
         count_launch();
-        k_heavy<<<grid_for(n, 256), 256, 0, st>>>(cnt, n, kSmallMax / kSortProbe, bc);
+        k_heavy<<<(unsigned)std::min<long long>(grid_for(n, 256), 152LL * 4), 256, 0, st>>>(
+            cnt, n, kSmallMax / kSortProbe, bc);
         count_launch();
         KC_TRY(cudaGetLastError(), "row classes");
         BuildCtl hbc;
