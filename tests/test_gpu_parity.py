@@ -273,6 +273,9 @@ def test_invalid_inputs_are_rejected(torch_cuda):
     with pytest.raises(K.KCoreError):
         K.Graph.from_coo(3, np.array([0], np.int32), np.array([1], np.int32),
                          options=K.default_options(t_hi=4096))
+    with pytest.raises(K.KCoreError):
+        K.Graph.from_coo(3, np.array([0], np.int32), np.array([1], np.int32),
+                         options=K.default_options(build_sort=2))
 
 
 def test_repeated_runs_identical(torch_cuda):
