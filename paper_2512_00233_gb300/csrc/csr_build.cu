@@ -84,6 +84,42 @@ struct Temp {
     }
 };
 
+// Build state on the device: the error flag and the class lists of the rows
+// that one thread does not sort.
+struct BuildCtl {
+    int bad;               // an id or offset out of range
+    unsigned n_mid, n_big, n_huge;
+    unsigned long long huge_entries;
+    unsigned long long entries, heavy;  // all counted entries; those in rows above kSmallMax
+};
+
+// Rows longer than kSmallMax, listed by size class (row u of length len).
+__device__ __forceinline__ void classify_row(long long u, uint32_t len, int* mid, int* big, int* huge,
+                                             BuildCtl* bc) {
+    if (len <= (uint32_t)kSmallMax) return;
+    if (len <= (uint32_t)kMidMax) {
+        mid[atomicAdd(&bc->n_mid, 1u)] = (int)u;
+    } else if (len <= (uint32_t)kBigMax) {
+        big[atomicAdd(&bc->n_big, 1u)] = (int)u;
+    } else {
+        huge[atomicAdd(&bc->n_huge, 1u)] = (int)u;
+        atomicAdd(&bc->huge_entries, (unsigned long long)len);
+    }
+}
+
+// Work a scan's down-sweep does on each input element: nothing, or (for the
+// row offsets) listing the long rows, whose lengths are the scanned counts.
+struct NoEpi {
+    __device__ __forceinline__ void operator()(long long, uint32_t) const {}
+};
+struct ClassifyEpi {
+    int *mid, *big, *huge;
+    BuildCtl* bc;
+    __device__ __forceinline__ void operator()(long long u, uint32_t len) const {
+        classify_row(u, len, mid, big, huge, bc);
+    }
+};
+
 // ------------------------------------------------------------------ scan
 constexpr int kScanT = 512, kScanI = 8, kScanTile = kScanT * kScanI;
 
@@ -158,9 +194,9 @@ struct ReadU32 {
     __device__ unsigned long long operator()(long long i) const { return p[i]; }
 };
 
-template <typename Out>
+template <typename Out, typename Epi = NoEpi>
 cudaError_t exclusive_scan4(const uint32_t* in, long long N, Out* out, bool with_total, cudaStream_t st,
-                            Temp* tmp);
+                            Temp* tmp, Epi epi = Epi());
 
 // Block sums and their offsets of one scan level (from `tmp` when given).
 inline cudaError_t scan_scratch(long long nb, unsigned long long** bsum, unsigned long long** boff,
@@ -222,12 +258,16 @@ __global__ void __launch_bounds__(kVecT) k_scan_reduce4(const uint32_t* __restri
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-template <typename Out>
+template <typename Out, typename Epi>
 __global__ void __launch_bounds__(kVecT) k_scan_down4(const uint32_t* __restrict__ in, long long N,
                                                       const unsigned long long* boff, Out* out,
-                                                      int write_total) {
+                                                      int write_total, Epi epi) {
     const long long i = (long long)blockIdx.x * kVecTile + threadIdx.x * 4;
     const uint4 v = load4(in, i, N);
+    if (i < N) epi(i, v.x);
+    if (i + 1 < N) epi(i + 1, v.y);
+    if (i + 2 < N) epi(i + 2, v.z);
+    if (i + 3 < N) epi(i + 3, v.w);
     unsigned long long tot;
     const unsigned long long b0 = boff ? boff[blockIdx.x] : 0ull;
     const unsigned long long r0 = block_excl_scan((unsigned long long)v.x + v.y + v.z + v.w, &tot) + b0;
@@ -272,13 +312,13 @@ cudaError_t exclusive_scan(F f, long long N, Out* out, bool with_total, cudaStre
     return e;
 }
 
-template <typename Out>
+template <typename Out, typename Epi>
 cudaError_t exclusive_scan4(const uint32_t* in, long long N, Out* out, bool with_total, cudaStream_t st,
-                            Temp* tmp) {
+                            Temp* tmp, Epi epi) {
     const long long nb = (N + kVecTile - 1) / kVecTile;
     if (nb == 1) {
         k_scan_down4<<<1, kVecT, 0, st>>>(in, N, (const unsigned long long*)nullptr, out,
-                                          with_total ? 1 : 0);
+                                          with_total ? 1 : 0, epi);
         count_launch();
         return cudaGetLastError();
     }
@@ -290,7 +330,7 @@ cudaError_t exclusive_scan4(const uint32_t* in, long long N, Out* out, bool with
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan(ReadU64{bsum}, nb, boff, false, st, tmp);
     if (e == cudaSuccess) {
-        k_scan_down4<<<(unsigned)nb, kVecT, 0, st>>>(in, N, boff, out, with_total ? 1 : 0);
+        k_scan_down4<<<(unsigned)nb, kVecT, 0, st>>>(in, N, boff, out, with_total ? 1 : 0, epi);
         count_launch();
         e = cudaGetLastError();
     }
@@ -310,15 +350,6 @@ size_t scan_scratch_bytes(long long N) {
 }
 
 // ------------------------------------------------------------------ count / scatter
-// Build state on the device: the error flag and the class lists of the rows
-// that one thread does not sort.
-struct BuildCtl {
-    int bad;               // an id or offset out of range
-    unsigned n_mid, n_big, n_huge;
-    unsigned long long huge_entries;
-    unsigned long long entries, heavy;  // all counted entries; those in rows above kSmallMax
-};
-
 // The samples of every step-th run of 256 (step 1: all of them); runs keep
 // the reads coalesced when only a share of the samples is counted.
 __global__ void k_count_coo(const int* __restrict__ src, const int* __restrict__ dst, long long S,
@@ -513,16 +544,7 @@ __global__ void k_classify(int n, const uint32_t* __restrict__ off, int* __restr
                            int* __restrict__ big, int* __restrict__ huge, BuildCtl* bc) {
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
          u += (long long)gridDim.x * blockDim.x) {
-        const uint32_t len = off[u + 1] - off[u];
-        if (len <= (uint32_t)kSmallMax) continue;
-        if (len <= (uint32_t)kMidMax) {
-            mid[atomicAdd(&bc->n_mid, 1u)] = (int)u;
-        } else if (len <= (uint32_t)kBigMax) {
-            big[atomicAdd(&bc->n_big, 1u)] = (int)u;
-        } else {
-            huge[atomicAdd(&bc->n_huge, 1u)] = (int)u;
-            atomicAdd(&bc->huge_entries, (unsigned long long)len);
-        }
+        classify_row(u, off[u + 1] - off[u], mid, big, huge, bc);
     }
 }
 
@@ -920,18 +942,45 @@ __global__ void k_huge_back(const int* __restrict__ huge, unsigned nh,
 }
 
 // ------------------------------------------------------------------ compaction
-// Rows of at most 32 entries: one thread each; the listed larger rows: one warp.
+// Rows of at most 32 entries: a warp takes 32 consecutive rows and walks their
+// distinct entries together, one entry per lane per step (the owner row found
+// by bisection over the lanes' prefix sums), so that reads and writes are
+// contiguous.  The listed larger rows: one warp each (k_compact_list).
 template <typename Off>
 __global__ void k_compact_small(int n, const uint32_t* __restrict__ off,
                                 const uint32_t* __restrict__ seg, const uint32_t* __restrict__ ucnt,
                                 const Off* __restrict__ rp, int* __restrict__ col) {
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
-         u += (long long)gridDim.x * blockDim.x) {
-        if (off[u + 1] - off[u] > (uint32_t)kSmallMax) continue;
-        const uint32_t c = ucnt[u];
-        const uint32_t* s = seg + off[u];
-        int* d = col + (long long)rp[u];
-        for (uint32_t i = 0; i < c; i++) d[i] = (int)s[i];
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long base = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * 32; base < n;
+         base += warps * 32) {
+        const long long u = base + lane;
+        uint32_t c = 0, o = 0;
+        long long r = 0;
+        if (u < n) {
+            o = off[u];
+            if (off[u + 1] - o <= (uint32_t)kSmallMax) c = ucnt[u];
+            r = (long long)rp[u];
+        }
+        uint32_t inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += t;
+        }
+        const uint32_t excl = inc - c, total = __shfl_sync(kFull, inc, 31);
+        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            int L = 0;  // the last lane whose first entry is at or before q
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(kFull, excl, L + step);
+                if (e <= q) L += step;
+            }
+            const uint32_t eL = __shfl_sync(kFull, excl, L), oL = __shfl_sync(kFull, o, L);
+            const long long rL = __shfl_sync(kFull, r, L);
+            if (q < total) col[rL + (q - eL)] = (int)seg[oL + (q - eL)];
+        }
     }
 }
 
@@ -1171,19 +1220,26 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
                        2 * scan_scratch_bytes(n)),
            "temporaries");
     KC_TRY(tmp.get(&off, (size_t)nn + 1), "row offsets");
-    KC_TRY(exclusive_scan(ReadU32{cnt}, n, off, true, st, &tmp), "offset scan");
-    BuildCtl hbc;
     KC_TRY(tmp.get(&seg, (size_t)N), "segments");
     KC_TRY(tmp.get(&ucnt, (size_t)nn), "distinct counts");
     KC_TRY(tmp.get(&mid, (size_t)nn), "row lists");
     KC_TRY(tmp.get(&big, nbig), "row lists");
     KC_TRY(tmp.get(&huge, nhuge), "row lists");
-    // the size classes, copied to the host while the scatter and the small
-    // sorts run: the host waits on the copy, not on the stream
-    if (n > 0) {
-        k_classify<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, mid, big, huge, bc);
-        count_launch();
-        KC_TRY(cudaGetLastError(), "classify rows");
+    BuildCtl hbc;
+    // offsets, and the size classes of the long rows (listed by the scan's
+    // down-sweep when the arrays allow its vector path, else by k_classify),
+    // copied to the host while the scatter and the small sorts run: the host
+    // waits on the copy, not on the stream
+    if (n > 0 && ((reinterpret_cast<uintptr_t>(cnt) | reinterpret_cast<uintptr_t>(off)) % 16 == 0)) {
+        KC_TRY(exclusive_scan4(cnt, n, off, true, st, &tmp, ClassifyEpi{mid, big, huge, bc}),
+               "offset scan");
+    } else {
+        KC_TRY(exclusive_scan(ReadU32{cnt}, n, off, true, st, &tmp), "offset scan");
+        if (n > 0) {
+            k_classify<<<grid_for(n, 256), 256, 0, st>>>((int)n, off, mid, big, huge, bc);
+            count_launch();
+            KC_TRY(cudaGetLastError(), "classify rows");
+        }
     }
     ClassRead cr;
     KC_TRY(pinned_get((void**)&cr.h, sizeof(BuildCtl)), "pinned buffer");
