@@ -942,45 +942,18 @@ __global__ void k_huge_back(const int* __restrict__ huge, unsigned nh,
 }
 
 // ------------------------------------------------------------------ compaction
-// Rows of at most 32 entries: a warp takes 32 consecutive rows and walks their
-// distinct entries together, one entry per lane per step (the owner row found
-// by bisection over the lanes' prefix sums), so that reads and writes are
-// contiguous.  The listed larger rows: one warp each (k_compact_list).
+// Rows of at most 32 entries: one thread each; the listed larger rows: one warp.
 template <typename Off>
 __global__ void k_compact_small(int n, const uint32_t* __restrict__ off,
                                 const uint32_t* __restrict__ seg, const uint32_t* __restrict__ ucnt,
                                 const Off* __restrict__ rp, int* __restrict__ col) {
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long base = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * 32; base < n;
-         base += warps * 32) {
-        const long long u = base + lane;
-        uint32_t c = 0, o = 0;
-        long long r = 0;
-        if (u < n) {
-            o = off[u];
-            if (off[u + 1] - o <= (uint32_t)kSmallMax) c = ucnt[u];
-            r = (long long)rp[u];
-        }
-        uint32_t inc = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, inc, d);
-            if (lane >= d) inc += t;
-        }
-        const uint32_t excl = inc - c, total = __shfl_sync(kFull, inc, 31);
-        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-            const uint32_t q = q0 + lane;
-            int L = 0;  // the last lane whose first entry is at or before q
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t e = __shfl_sync(kFull, excl, L + step);
-                if (e <= q) L += step;
-            }
-            const uint32_t eL = __shfl_sync(kFull, excl, L), oL = __shfl_sync(kFull, o, L);
-            const long long rL = __shfl_sync(kFull, r, L);
-            if (q < total) col[rL + (q - eL)] = (int)seg[oL + (q - eL)];
-        }
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x) {
+        if (off[u + 1] - off[u] > (uint32_t)kSmallMax) continue;
+        const uint32_t c = ucnt[u];
+        const uint32_t* s = seg + off[u];
+        int* d = col + (long long)rp[u];
+        for (uint32_t i = 0; i < c; i++) d[i] = (int)s[i];
     }
 }
 
