@@ -534,12 +534,13 @@ __global__ void k_sort_small(int n, const uint32_t* __restrict__ off, uint32_t* 
             ucnt[u] = thread_sort_row<16>(s, len);
         } else if (len <= kSmallMax) {
             ucnt[u] = thread_sort_row<32>(s, len);
-        }  // longer rows: listed by k_classify, sorted by the class kernels
+        }  // longer rows: listed by class after the offset scan, sorted by the class kernels
     }
 }
 
-// Lists the rows longer than kSmallMax by size class (from the offsets alone,
-// so that the host can read the classes while the scatter runs).
+// Lists the rows longer than kSmallMax by size class from the offsets alone,
+// so that the host can read the classes while the scatter runs.  (Used when
+// the offset scan cannot take its vector path, which lists them itself.)
 __global__ void k_classify(int n, const uint32_t* __restrict__ off, int* __restrict__ mid,
                            int* __restrict__ big, int* __restrict__ huge, BuildCtl* bc) {
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n;
