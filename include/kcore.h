@@ -106,7 +106,8 @@ typedef struct kcore_options {
                                -1 = rows counted, filled and sorted one by one;
                                0 (default) = the sort when the input has at least
                                2^18 samples, 2*samples >= 8n, and rows of more
-                               than 32 entries hold half of the entries or more.
+                               than 32 entries hold half of the entries or more
+                               (estimated from every 16th run of 256 samples).
                                The cleaned graph is the same either way.          */
 } kcore_options;
 
