@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "kc_common.cuh"
+#include "ranges.h"
 
 namespace kc {
 
@@ -49,57 +50,6 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
         .count();
 }
-
-// First-fit allocator of [0, cap) ranges with coalescing on free.
-class Ranges {
-  public:
-    void reset(long long cap) {
-        free_.clear();
-        if (cap > 0) free_[0] = cap;
-        cap_ = cap;
-    }
-    long long take(long long len) {
-        if (len <= 0) return 0;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= len) {
-                const long long at = it->first, rest = it->second - len;
-                free_.erase(it);
-                if (rest > 0) free_[at + len] = rest;
-                used_ += len;
-                peak_ = std::max(peak_, used_);
-                return at;
-            }
-        }
-        return -1;
-    }
-    void give(long long at, long long len) {
-        if (len <= 0) return;
-        used_ -= len;
-        auto next = free_.lower_bound(at);
-        if (next != free_.end() && at + len == next->first) {
-            len += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == at) {
-                prev->second += len;
-                return;
-            }
-        }
-        free_[at] = len;
-    }
-    long long largest() const {
-        long long b = 0;
-        for (auto& kv : free_) b = std::max(b, kv.second);
-        return b;
-    }
-    long long peak() const { return peak_; }
-
-  private:
-    std::map<long long, long long> free_;
-    long long cap_ = 0, used_ = 0, peak_ = 0;
-};
 
 struct Request {
     uint64_t ticket = 0;
