@@ -29,7 +29,7 @@ def _worker(rank, ws, port, out):
 def test_two_rank_aggregation_takes_max_time_and_sums_units():
     ws = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:   # no fork of this threaded process
         out = mgr.dict()
         mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
