@@ -267,6 +267,55 @@ def test_sync_round_step_semantics():
         prev = est
 
 
+def test_sync_round_step_semantics_refined():
+    """Refined rule (Sec. IV, Further Optimizations, read as the conjunction
+    new_u < est(v) <= old_u and decided after the round's updates, the extra
+    barrier that passage mentions): every round's frontier is recomputed here
+    from two consecutive rounds' estimates, independently of the oracle's
+    bookkeeping, and must equal the oracle's next frontier.  The graphs hold
+    many neighbours whose post-round estimate equals old_u exactly (the
+    boundary of the <= ), and many whose pre-round value differs from the
+    post-round one, so reading '<' for '<=', or the pre-round snapshot for the
+    post-round value, changes a frontier size."""
+    cases = [graphgen.rmat(1 << 11, 8 << 11, 0.57, 0.19, 0.19, seed=9),
+             graphgen.union(graphgen.rmat(1 << 10, 6 << 10, 0.45, 0.22, 0.22, seed=21),
+                            graphgen.planted(1 << 10, 60, 0.5, seed=22)),
+             graphgen.damaged_grid(40, seed=23)]
+    boundary_hits = 0
+    stale_differs = 0
+    for g in cases:
+        rp, col = oracle.csr_build(g.n, g.src, g.dst)
+        n = g.n
+        deg = np.diff(rp)
+        total, _, fr, ch = oracle.montresor_sync(n, rp, col, refined=True, record=1000)
+        assert total >= 1 and fr[0] == n
+        prev = deg.astype(np.int32)
+        for s in range(total):
+            _, est, _, _ = oracle.montresor_sync(n, rp, col, max_rounds=s + 1, refined=True)
+            changed = np.nonzero(est != prev)[0]
+            assert (est <= prev).all()
+            assert changed.shape[0] == ch[s]
+            act = set()
+            for u in changed:
+                nbrs = col[rp[u]:rp[u + 1]]
+                # the round computes from the previous round's estimates
+                assert est[u] == refimpl.hindex_sorted(prev[nbrs], prev[u])
+                old_u, new_u = int(prev[u]), int(est[u])
+                for v in nbrs:
+                    x = int(est[v])          # v's value after this round
+                    if new_u < x <= old_u:
+                        act.add(int(v))
+                    boundary_hits += int(x == old_u)
+                    stale_differs += int((new_u < int(prev[v]) <= old_u) != (new_u < x <= old_u))
+            if s + 1 < total:
+                assert len(act) == fr[s + 1], (g.name, s)
+            else:
+                assert len(act) == 0
+            prev = est
+    # the cases exercise both readings that a slip would change
+    assert boundary_hits > 100 and stale_differs > 10
+
+
 def test_sync_start_from_degree_matters_on_cycle():
     n = 9
     rp, col = csr_of(n, cycle(n))
