@@ -7,20 +7,25 @@
 // entry point serves them.  Its working memory (control block, frontier
 // bitmaps and lists) is one fixed array compiled into the library; the
 // estimates live in the caller's output buffer.  The array holds
-// KCORE_NOALLOC_MAX_N vertices and stays resident on every GPU that loads
-// the library until the process exits.
+// KCORE_NOALLOC_MAX_N vertices and stays resident on every GPU where it has
+// been loaded until the process exits.  With the CUDA runtime's lazy module
+// loading (the default since CUDA 12.2) the array is reserved on a device the
+// first time this file's device code is used there, i.e. on the first call,
+// and the kernels are loaded on their first launch; a call with n = 0 does
+// only that loading, so a caller can make it before it reserves the rest of
+// the device.
 //
 // In host code `g_noalloc_scratch` names a host-side stand-in, not device
-// memory: the device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and passed to the kernels.
-// Every call shares the array; each call clears what must start at zero, and
-// calls that overlap on the GPU race on it.
+// memory: the device address is looked up on every call with
+// cudaGetSymbolAddress (with the caller's device current; cheap once the
+// module is loaded, and never stale after a context is re-created) and passed
+// to the kernels.  Every call shares the array; each call clears what must
+// start at zero, and calls that overlap on the GPU race on it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "kc_common.cuh"
@@ -42,47 +47,33 @@ constexpr size_t kScratchBytes = kCtlBytes + kParities * (kBitmapBytes + kListBy
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[64] = {};  // device address of the array, per device ordinal
-
+// Device address of the array on the current device.  Loads this file's
+// module there if it is not loaded yet (which reserves the array).
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = (unsigned char*)g_addr[dev];
+    *out = (unsigned char*)p;
     return cudaSuccess;
 }
 
-// Estimates start at the degrees (tier in the top bits), every vertex joins
-// the first frontier in its tier's region, and rows are checked: a malformed
-// CSR sets the status, which ends the sweep kernel before its first sweep.
+// Estimates start at the degrees (tier in the top bits) and every vertex joins
+// the first frontier in its tier's region.  Offsets are checked here (row
+// bounds inside [0, nnz], rows in order); a bad row sets the status, which
+// ends the sweep kernel before its first sweep, and counts as degree 0.
 template <typename Off>
-__global__ void k_noalloc_init(const Off* __restrict__ rp, const int* __restrict__ col, int n,
-                               long long nnz, int t_lo, int t_hi, uint32_t* __restrict__ est,
-                               int* __restrict__ list0, SweepCtl* ctl) {
+__global__ void k_noalloc_init(const Off* __restrict__ rp, int n, long long nnz, int t_lo, int t_hi,
+                               uint32_t* __restrict__ est, int* __restrict__ list0, SweepCtl* ctl) {
     const int lane = threadIdx.x & 31;
     for (long long v0 = blockIdx.x * (long long)blockDim.x; v0 < n;
          v0 += (long long)gridDim.x * blockDim.x) {
         const long long v = v0 + threadIdx.x;
         const bool valid = v < n;
-        long long b = 0, e = 0;
         int tier = -1;
         if (valid) {
-            b = (long long)rp[v];
-            e = (long long)rp[v + 1];
-            bool ok = e >= b && b >= 0 && e <= nnz && (v > 0 || b == 0);
-            for (long long j = b; ok && j < e; j++) {
-                const int w = col[j];
-                ok = (unsigned)w < (unsigned)n && w != (int)v && (j == b || col[j - 1] < w);
-            }
+            const long long b = (long long)rp[v];
+            const long long e = (long long)rp[v + 1];
+            const bool ok = e >= b && b >= 0 && e <= nnz && (v > 0 || b == 0);
             if (!ok) atomicCAS(&ctl->status, 0, (int)KCORE_ERR_INVALID);
             const long long d = ok ? e - b : 0;
             tier = d <= t_lo ? 0 : (d <= t_hi ? 1 : 2);
@@ -100,6 +91,43 @@ __global__ void k_noalloc_init(const Off* __restrict__ rp, const int* __restrict
             }
         }
     }
+}
+
+// The entries of a clean CSR, checked edge-parallel (a hub row is spread over
+// many warps): every id in [0, n), no loop, each row strictly increasing.  A
+// warp takes 32 consecutive entries; lane 0 finds the row of the first by
+// bisection of row_ptr, and each lane walks forward to its own row.  Any
+// failure sets the status.  Reads stay inside row_ptr[0, n] and col[0, nnz)
+// even when the offsets are malformed (the init kernel reports those).
+template <typename Off>
+__global__ void k_noalloc_check(const Off* __restrict__ rp, const int* __restrict__ col, int n,
+                                long long nnz, SweepCtl* ctl) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    bool ok = true;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w * 32 < nnz;
+         w += warps) {
+        const long long j0 = w * 32, j = j0 + lane;
+        long long r = 0;
+        if (lane == 0) {  // last row r in [0, n - 1] with rp[r] <= j0
+            long long lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if ((long long)rp[mid] <= j0) lo = mid;
+                else hi = mid - 1;
+            }
+            r = lo;
+        }
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (j < nnz) {
+            while (r < n - 1 && (long long)rp[r + 1] <= j) r++;
+            const int x = col[j];
+            const long long b = (long long)rp[r];
+            ok = ok && (unsigned)x < (unsigned)n && x != (int)r;
+            if (j > 0 && j > b) ok = ok && col[j - 1] < x;
+        }
+    }
+    if (__any_sync(0xffffffffu, !ok) && lane == 0) atomicCAS(&ctl->status, 0, (int)KCORE_ERR_INVALID);
 }
 
 __global__ void k_noalloc_bitmap(uint32_t* bm0, long long words, int n) {
@@ -125,13 +153,31 @@ extern "C" kcore_status kcore_run_noalloc(int64_t n, const void* row_ptr, int32_
                                            std::to_string(kMaxN) + "] (KCORE_NOALLOC_MAX_N)");
     if (row_ptr_bytes != 4 && row_ptr_bytes != 8)
         return fail(KCORE_ERR_INVALID, "kcore_run_noalloc: row_ptr_bytes must be 4 or 8");
-    if (n == 0) return KCORE_OK;
+    unsigned char* base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess)
+        return cuda_status(e, "kcore_run_noalloc: cudaGetSymbolAddress (loading the module that "
+                              "holds the fixed working array)");
+    if (n == 0) {
+        // preparation: load every kernel this entry point launches, so that
+        // later calls load nothing (lazy loading would do it on first use)
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_noalloc_init<int>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_noalloc_init<long long>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_noalloc_check<int>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_noalloc_check<long long>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_noalloc_bitmap);
+        kcore_options o;
+        kcore_default_options(&o);
+        int grid = 0;
+        for (int off64 = 0; off64 < 2 && e == cudaSuccess; off64++)
+            e = sweep_max_grid(o.block, o.t_lo, o.t_hi, off64, &grid);
+        if (e != cudaSuccess) return cuda_status(e, "kcore_run_noalloc: loading its kernels");
+        return KCORE_OK;
+    }
     if (!row_ptr || !col_idx || !coreness_out)
         return fail(KCORE_ERR_INVALID, "kcore_run_noalloc: NULL pointer");
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    unsigned char* base = nullptr;
-    cudaError_t e = scratch_address(&base);
-    if (e != cudaSuccess) return cuda_status(e, "kcore_run_noalloc: cudaGetSymbolAddress");
     SweepCtl* ctl = (SweepCtl*)base;
     uint32_t* bitmap[kParities];
     int* list[kParities];
@@ -155,17 +201,24 @@ extern "C" kcore_status kcore_run_noalloc(int64_t n, const void* row_ptr, int32_
     if (e == cudaSuccess) e = cudaMemsetAsync(bitmap[1], 0, sizeof(uint32_t) * words, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bitmap[2], 0, sizeof(uint32_t) * words, st);
     if (e != cudaSuccess) return cuda_status(e, "kcore_run_noalloc: clear");
-    const int g = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    const int g = (int)std::min<long long>((n + 255) / 256, (long long)sm_count() * 8);
     k_noalloc_bitmap<<<g, 256, 0, st>>>(bitmap[0], words, (int)n);
     count_launch();
     uint32_t* est = (uint32_t*)coreness_out;
-    if (row_ptr_bytes == 8)
-        k_noalloc_init<<<g, 256, 0, st>>>((const long long*)row_ptr, col_idx, (int)n, nnz, o.t_lo,
-                                          o.t_hi, est, list[0], ctl);
-    else
-        k_noalloc_init<<<g, 256, 0, st>>>((const int*)row_ptr, col_idx, (int)n, nnz, o.t_lo, o.t_hi,
+    const int gc = (int)std::max<long long>(1, std::min<long long>((nnz + 255) / 256,
+                                                                   (long long)sm_count() * 8));
+    if (row_ptr_bytes == 8) {
+        k_noalloc_init<<<g, 256, 0, st>>>((const long long*)row_ptr, (int)n, nnz, o.t_lo, o.t_hi,
                                           est, list[0], ctl);
+        if (nnz > 0)
+            k_noalloc_check<<<gc, 256, 0, st>>>((const long long*)row_ptr, col_idx, (int)n, nnz, ctl);
+    } else {
+        k_noalloc_init<<<g, 256, 0, st>>>((const int*)row_ptr, (int)n, nnz, o.t_lo, o.t_hi, est,
+                                          list[0], ctl);
+        if (nnz > 0) k_noalloc_check<<<gc, 256, 0, st>>>((const int*)row_ptr, col_idx, (int)n, nnz, ctl);
+    }
     count_launch();
+    if (nnz > 0) count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "kcore_run_noalloc: init");
 
