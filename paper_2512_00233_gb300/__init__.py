@@ -12,12 +12,14 @@ import ctypes
 import numpy as np
 
 from ._lib import (KCORE_ASYNC, KCORE_GRAPH, KCORE_SIMPLE, KCORE_ERR_AGAIN, KCORE_ERR_CANCELLED, KCORE_ERR_INVALID,
+                   KCORE_ERR_OOM, KCORE_ERR_CUDA,
                    KCORE_ERR_NOT_CONVERGED, KCORE_ERR_TIMEOUT, KCORE_IN_CLEAN, KCORE_IN_DEVICE,
                    KCORE_OK, KCORE_OUT_DEVICE, KCORE_PENDING, KCORE_REFINED, KCORE_SYNC_MODE,
-                   SIGNATURES, BatchStats, KCoreError, Options, RunStats, ServeOptions, check, lib)
+                   SIGNATURES, BatchStats, KCoreError, Options, RunStats, ServeOptions, TicketInfo,
+                   check, lib)
 
 __all__ = ["Graph", "BatchEngine", "default_options", "default_serve_options", "lib",
-           "KCoreError", "Options", "RunStats", "version"]
+           "KCoreError", "Options", "RunStats", "TicketInfo", "version"]
 
 
 def version() -> str:
@@ -214,6 +216,17 @@ class Graph:
                                        ctypes.byref(cnt)), "kcore_sweep_detail")
         return r[:cnt.value], dec[:cnt.value]
 
+    def trace_tiers(self, cap: int = 1 << 16):
+        """Per-sweep frontier size and degree sum per degree tier: two arrays of
+        shape (sweeps, 3), tiers thread / warp / CTA."""
+        f = np.zeros(3 * cap, np.int64)
+        d = np.zeros(3 * cap, np.int64)
+        cnt = ctypes.c_int64()
+        check(lib().kcore_sweep_tiers(self._h, f.ctypes.data, d.ctypes.data, cap,
+                                      ctypes.byref(cnt)), "kcore_sweep_tiers")
+        k = cnt.value
+        return f[:3 * k].reshape(k, 3), d[:3 * k].reshape(k, 3)
+
     def row_ptr_host(self):
         """row_ptr of the cleaned graph as a numpy array."""
         rp = np.empty(self.n + 1, dtype=np.int64 if self.row_ptr_bytes == 8 else np.int32)
@@ -279,6 +292,19 @@ class BatchEngine:
         if st == KCORE_OK:
             return st, (out[:n] if out is not None else None)
         return st, None
+
+    def poll_info(self, ticket: int, n: int | None = None, timeout_us: int = -1):
+        """(status, coreness or None, info dict or None): kcore_poll_info.  The
+        info (times on the monotonic clock of time.perf_counter, launch
+        numbers) is filled on every return but KCORE_PENDING."""
+        out = np.empty(max(n or 0, 1), dtype=np.int32) if n is not None else None
+        info = TicketInfo()
+        st = lib().kcore_poll_info(self._h, ticket, out.ctypes.data if out is not None else None,
+                                   timeout_us, ctypes.byref(info))
+        if st == KCORE_PENDING:
+            return st, None, None
+        d = {k: getattr(info, k) for k, _ in TicketInfo._fields_}
+        return st, (out[:n] if (st == KCORE_OK and out is not None) else None), d
 
     def cancel(self, ticket: int) -> int:
         return lib().kcore_cancel(self._h, ticket)

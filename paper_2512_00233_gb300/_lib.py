@@ -73,7 +73,14 @@ class BatchStats(ctypes.Structure):
                 ("arena_used_peak", c_i64), ("latency_p50_ms", ctypes.c_double),
                 ("latency_p99_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
                 ("admit_s", ctypes.c_double), ("sweep_s", ctypes.c_double),
-                ("retire_s", ctypes.c_double), ("admissions", c_i64)]
+                ("retire_s", ctypes.c_double), ("admissions", c_i64),
+                ("admitted_while_busy", c_i64)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("admit_launch", c_i64), ("retire_launch", c_i64),
+                ("resident_at_admit", c_i64)]
 
 
 # name: (restype, argtypes)
@@ -92,6 +99,7 @@ SIGNATURES = {
     "kcore_stats": (c_i32, [c_vp, ctypes.POINTER(RunStats)]),
     "kcore_sweep_trace": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "kcore_sweep_detail": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
+    "kcore_sweep_tiers": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "kcore_run_from": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_u32, c_vp]),
     "kcore_destroy": (None, [c_vp]),
     "kcore_run_noalloc": (c_i32, [c_i64, c_vp, c_i32, c_vp, c_vp, c_vp]),
@@ -100,6 +108,7 @@ SIGNATURES = {
     "kcore_submit": (c_i32, [c_vp, c_i64, c_vp, c_i32, c_vp, c_u32, ctypes.POINTER(c_u64)]),
     "kcore_submit_coo": (c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_u32, ctypes.POINTER(c_u64)]),
     "kcore_poll": (c_i32, [c_vp, c_u64, c_vp, c_i64]),
+    "kcore_poll_info": (c_i32, [c_vp, c_u64, c_vp, c_i64, ctypes.POINTER(TicketInfo)]),
     "kcore_cancel": (c_i32, [c_vp, c_u64]),
     "kcore_batch_step": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "kcore_batch_stats_get": (c_i32, [c_vp, ctypes.POINTER(BatchStats)]),
@@ -108,6 +117,10 @@ SIGNATURES = {
     "kcore_version": (ctypes.c_char_p, []),
     "kcore_kernel_launches": (c_i64, []),
     "kcore_release_cached_memory": (None, []),
+    # test hooks (include/kcore_test.h)
+    "kcore_test_fail_alloc": (None, [c_i64]),
+    "kcore_test_alloc_count": (c_i64, []),
+    "kcore_test_pool_usage": (c_i32, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
 }
 
 _lib = None

@@ -222,6 +222,28 @@ kcore_status upload(const T* host, size_t count, cudaStream_t st, T** dev) {
     return KCORE_OK;
 }
 
+// The update lists of synchronous mode, allocated on the first synchronous
+// run: both or neither (a half-allocated pair is released again).
+kcore_status ensure_sync_buffers(kcore_graph* g, cudaStream_t st) {
+    if (g->upd_list && g->upd_val) return KCORE_OK;
+    std::string err;
+    const int64_t n = g->csr.n;
+    kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
+    if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
+    if (s == KCORE_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+        s = KCORE_ERR_CUDA;
+        err = "synchronous-mode buffers";
+    }
+    if (s != KCORE_OK) {
+        dfree(g->upd_list, st);
+        dfree(g->upd_val, st);
+        g->upd_list = nullptr;
+        g->upd_val = nullptr;
+        return fail(s, err);
+    }
+    return KCORE_OK;
+}
+
 kcore_status wait_run(kcore_graph* g) {
     if (!g->pending) return g->last_status;
     g->pending = false;
@@ -569,12 +591,9 @@ kcore_status kcore_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, vo
         return fail(KCORE_ERR_INVALID, "KCORE_GRAPH needs a device output (KCORE_OUT_DEVICE)");
     if (g->pending) wait_run(g);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    std::string err;
-    if ((flags & KCORE_SYNC_MODE) && !g->upd_list) {
-        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
-        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
-        if (s == KCORE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = KCORE_ERR_CUDA;
-        if (s != KCORE_OK) return fail(s, err);
+    if (flags & KCORE_SYNC_MODE) {
+        kcore_status s = ensure_sync_buffers(g, st);
+        if (s != KCORE_OK) return s;
     }
     kcore_status s = (flags & KCORE_GRAPH) ? graph_run(g, coreness_out, flags, st)
                                           : enqueue_run(g, coreness_out, flags, st, false);
@@ -596,11 +615,9 @@ kcore_status kcore_run_from(kcore_graph* g, const int32_t* start, const int32_t*
     if (flags & KCORE_GRAPH) return fail(KCORE_ERR_INVALID, "KCORE_GRAPH is not available with a warm start");
     if (g->pending) wait_run(g);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    std::string err;
-    if ((flags & KCORE_SYNC_MODE) && !g->upd_list) {
-        kcore_status s = dmalloc((void**)&g->upd_list, sizeof(int) * n, &err, st);
-        if (s == KCORE_OK) s = dmalloc((void**)&g->upd_val, sizeof(int) * n, &err, st);
-        if (s != KCORE_OK) return fail(s, err);
+    if (flags & KCORE_SYNC_MODE) {
+        kcore_status s = ensure_sync_buffers(g, st);
+        if (s != KCORE_OK) return s;
     }
     WarmStart w;
     int *tmp_start = nullptr, *tmp_front = nullptr;
@@ -730,6 +747,32 @@ kcore_status kcore_sweep_detail(kcore_graph* g, int64_t* entries_read, int64_t* 
         const long long* r = h.data() + kTraceCols * i;
         if (entries_read) entries_read[i] = r[kTrRead];
         if (decrease) decrease[i] = r[kTrDec];
+    }
+    if (count) *count = n;
+    return KCORE_OK;
+}
+
+kcore_status kcore_sweep_tiers(kcore_graph* g, int64_t* frontier, int64_t* degsum, int64_t cap,
+                               int64_t* count) {
+    if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
+    if (count) *count = 0;
+    std::vector<long long> h;
+    long long n = 0;
+    kcore_status s = trace_rows(g, cap, &h, &n);
+    if (s != KCORE_OK) return s;
+    for (long long i = 0; i < n; i++) {
+        const long long* r = h.data() + kTraceCols * i;
+        const long long w = r[kTrDegW], c = r[kTrDegC];
+        if (frontier) {
+            frontier[3 * i] = r[kTrF0];
+            frontier[3 * i + 1] = r[kTrF1];
+            frontier[3 * i + 2] = r[kTrF2];
+        }
+        if (degsum) {
+            degsum[3 * i] = r[kTrDegsum] - w - c;
+            degsum[3 * i + 1] = w;
+            degsum[3 * i + 2] = c;
+        }
     }
     if (count) *count = n;
     return KCORE_OK;

@@ -28,10 +28,13 @@ enum {
     kAccPushes = 3,
     kAccSkipped = 4,  // adjacency entries not read thanks to an early exit
     kAccDec = 5,      // sum of estimate decreases
-    kAccN = 6
+    kAccDegW = 6,     // frontier degree sum of the warp tier
+    kAccDegC = 7,     // frontier degree sum of the CTA tier
+    kAccN = 8
 };
-// Columns of the per-sweep trace.
-enum { kTrFrontier = 0, kTrDegsum, kTrUpdates, kTrStart, kTrRead, kTrDec, kTraceCols };
+// Columns of the per-sweep trace (kTrF0..2: frontier size per degree tier).
+enum { kTrFrontier = 0, kTrDegsum, kTrUpdates, kTrStart, kTrRead, kTrDec, kTrF0, kTrF1, kTrF2,
+       kTrDegW, kTrDegC, kTraceCols };
 
 // Control block of the persistent sweep kernel (device memory).  Counter slot
 // s % 4 holds the frontier counts of sweep s; sweep s pushes into slot
@@ -141,6 +144,11 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
 cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,
                             cudaStream_t st);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// cached per device ordinal); grid-stride kernels size their grids from it.
+// 1 if the query fails (the launch that follows reports the error).
+int sm_count();
+
 // Number of kernels this library has launched in the process (all devices).
 void count_launch();
 long long launches();
@@ -151,6 +159,9 @@ kcore_status dmalloc(void** p, size_t bytes, std::string* err, cudaStream_t st =
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);  // free with cudaFreeAsync
 void dfree(void* p, cudaStream_t st = 0);
 constexpr size_t kPinnedBlock = 4096;
+// Test hook (kcore_test.h): true when this allocation request is the one the
+// injector was armed to fail.  Every allocation site asks once per request.
+bool alloc_fault();
 cudaError_t pinned_get(void** p, size_t bytes);
 void pinned_put(void* p);
 

@@ -57,7 +57,8 @@ def test_struct_layout_matches_header(tmp_path):
     """ctypes mirrors of the ABI structs have the C compiler's size and offsets."""
     import subprocess
     structs = {"kcore_options": K.Options, "kcore_run_stats": K.RunStats,
-               "kcore_serve_options": K.ServeOptions, "kcore_batch_stats": K.BatchStats}
+               "kcore_serve_options": K.ServeOptions, "kcore_batch_stats": K.BatchStats,
+               "kcore_ticket_info": K.TicketInfo}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kcore.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
