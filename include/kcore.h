@@ -247,6 +247,16 @@ kcore_status kcore_sweep_detail(kcore_graph* g, int64_t* entries_read, int64_t* 
                                 int64_t cap, int64_t* count);
 
 /*
+ * Per-tier columns of the same trace: for sweep s, frontier[3 s + q] is the
+ * number of vertices of degree tier q (0: degree <= t_lo, one thread each;
+ * 1: <= t_hi, one warp each; 2: above, one CTA each) in the sweep's frontier
+ * and degsum[3 s + q] their degree sum.  Arrays hold 3 * cap values; either may
+ * be NULL.  Same conventions as kcore_sweep_trace.
+ */
+kcore_status kcore_sweep_tiers(kcore_graph* g, int64_t* frontier, int64_t* degsum, int64_t cap,
+                               int64_t* count);
+
+/*
  * kcore_run_from -- the iteration started from caller-given upper bounds
  * instead of the degrees: dynamic core maintenance (Sec. VI names it as future
  * work; this is its local-iteration form).  The fixed point reached from any
@@ -288,9 +298,19 @@ void kcore_destroy(kcore_graph* g);
  * a real-time loop that must not stall on the allocator's implicit
  * synchronisation, code running inside another allocator's callback.  The
  * working memory is one fixed array compiled into the library, sized for
- * KCORE_NOALLOC_MAX_N vertices (about 19 MB), resident on every GPU that loads
- * the library until the process exits; the estimates live in coreness_out.
- * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * KCORE_NOALLOC_MAX_N vertices (about 19 MB); the estimates live in
+ * coreness_out.  No call allocates: no cudaMalloc, cudaFree or allocating
+ * library call.
+ *
+ * Where the array comes from: the CUDA runtime loads the library's device
+ * code lazily by default (CUDA_MODULE_LOADING=LAZY since CUDA 12.2), so the
+ * array, and the kernels this entry point launches, are loaded on a device
+ * the first time they are used there, and stay until the process exits.  A
+ * call with n = 0 does only that loading (the pointers may then be NULL):
+ * make it once per device, with that device current, before reserving the
+ * rest of the device memory; later calls then allocate nothing at all.  If
+ * the device has no room left for them, that first call returns ERR_OOM.
+ *
  *   n             0 <= n <= KCORE_NOALLOC_MAX_N; larger n gives ERR_INVALID.
  *   row_ptr       DEVICE pointer, n+1 offsets, int32 or int64 per
  *                 row_ptr_bytes (4 or 8), of a clean CSR: symmetric, rows
@@ -298,10 +318,12 @@ void kcore_destroy(kcore_graph* g);
  *   col_idx       DEVICE pointer, row_ptr[n] int32 vertex ids.
  *   coreness_out  DEVICE pointer, n int32, caller-owned; it also holds the
  *                 estimates while the call runs.
- * The call is synchronous on `cuda_stream` and returns the run's status
- * (ERR_INVALID for a malformed CSR, as kcore_run otherwise).  The first call
- * on each device looks the array's device address up (cudaGetSymbolAddress,
- * with that device current): make that first call before any stream capture.
+ * The call is synchronous: it reads row_ptr[n] back and waits for the run
+ * on `cuda_stream` before it returns, so it must not be called while that
+ * stream is being captured into a CUDA graph.  Returns the run's status:
+ * ERR_INVALID for offsets or entries that are not a clean CSR (ids outside
+ * [0, n), a self-loop, a row not strictly increasing: checked on the device
+ * before the first sweep), otherwise as kcore_run.
  * Every call shares the one array and finds the previous call's contents in
  * it; each call clears what must start at zero.  Calls that overlap on the GPU
  * (on two streams, or from two threads) race on the array: serialise them.
@@ -363,13 +385,42 @@ kcore_status kcore_submit_coo(kcore_batch* b, int64_t n, int64_t nnz, const int3
  */
 kcore_status kcore_poll(kcore_batch* b, uint64_t ticket, int32_t* coreness_out, int64_t timeout_us);
 
+/*
+ * Timing and placement of one request, for latency measurement and for
+ * checking that the engine overlaps work (continuous batching).  Times are
+ * seconds of the monotonic clock (CLOCK_MONOTONIC; the clock of
+ * std::chrono::steady_clock and of Python's time.perf_counter on Linux).
+ * Launch numbers count the engine's persistent sweep launches from 0: the
+ * request took part in launches [admit_launch, retire_launch).
+ */
+typedef struct kcore_ticket_info {
+    double  submit_s;        /* kcore_submit* accepted it (after copying)         */
+    double  admit_s;         /* placed into the arena                            */
+    double  done_s;          /* result ready (retired, cancelled or failed)      */
+    int64_t admit_launch;    /* first persistent launch it took part in          */
+    int64_t retire_launch;   /* launches run when it was retired                 */
+    int64_t resident_at_admit;  /* other graphs resident when it was placed      */
+} kcore_ticket_info;
+
+/*
+ * kcore_poll with the request's timing and placement: as kcore_poll, and on
+ * any return other than KCORE_PENDING (the ticket is then released), *info
+ * (may be NULL) gets the request's kcore_ticket_info.
+ */
+kcore_status kcore_poll_info(kcore_batch* b, uint64_t ticket, int32_t* coreness_out,
+                             int64_t timeout_us, kcore_ticket_info* info);
+
 /* Cancel a queued or running request; its slot is freed at the next chunk. */
 kcore_status kcore_cancel(kcore_batch* b, uint64_t ticket);
 
 /*
  * Drive the engine once (admit, one chunk of sweeps, retire) when it was
  * created with start_thread = 0.  *active gets the number of graphs resident
- * or queued afterwards.
+ * or queued afterwards.  An admission that fails before its graphs are placed
+ * (device memory, upload, cleaning) fails only those graphs (their tickets
+ * report the error; their memory is given back) and the step goes on with the
+ * resident graphs; an error of the sweep launch or of placement fails every
+ * resident graph and is returned here.
  */
 kcore_status kcore_batch_step(kcore_batch* b, int64_t* active);
 
@@ -384,6 +435,8 @@ typedef struct kcore_batch_stats {
                                             build, cleaning, placement), sweep
                                             launches, retirement (result copies) */
     int64_t admissions;              /* admission batches placed into the arena        */
+    int64_t admitted_while_busy;     /* graphs placed while other graphs were resident
+                                        and unfinished (continuous batching)           */
 } kcore_batch_stats;
 
 kcore_status kcore_batch_stats_get(kcore_batch* b, kcore_batch_stats* out);

@@ -12,9 +12,12 @@
 //      the coreness (the iteration's fixed point), copied out, ranges freed;
 //   2. admits queued graphs that fit: the whole admission batch is cleaned as
 //      one disjoint union (one device CSR-cleaning call), placed into a
-//      contiguous vertex range (one spare vertex at the end, so the last row
-//      has an end offset), its estimates set to the degrees and every vertex
-//      pushed into the current frontier.
+//      contiguous vertex range, its estimates set to the degrees and every
+//      vertex pushed into the current frontier.  Each graph is followed by a
+//      spare vertex of its own (isolated, never in a frontier), whose row_ptr
+//      slot holds the end of the graph's last row: the graph owns that slot,
+//      so placing another graph into a neighbouring freed range can never
+//      move the end of a resident graph's last row.
 // A graph admitted while others run joins at the next chunk.  The coreness is
 // unique and the iteration reaches it from any schedule, so each result is
 // the same alone or in any mix.
@@ -69,7 +72,8 @@ struct Request {
     const uint32_t* res = nullptr;
     long long r_off = -1;
     std::vector<uint32_t> result;
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    long long admit_launch = -1, retire_launch = -1, resident_at_admit = 0;
     // placement
     int slot = -1;
     long long v0 = 0, vlen = 0, e0 = 0, elen = 0;
@@ -86,8 +90,11 @@ __device__ __forceinline__ int slot_index(const long long* starts, int count, lo
 }
 
 // Places the cleaned union (vertices [0, nu), its own row_ptr/col) at arena
-// vertex V0 / entry E0, sets estimates and slots, and pushes every vertex into
-// the current frontier (list and bitmap parity pc, counter slot cs).
+// vertex V0 / entry E0, sets estimates and slots, and pushes every real vertex
+// into the current frontier (list and bitmap parity pc, counter slot cs).
+// Graph g holds union vertices [gstart[g], gstart[g+1] - 1) and its spare
+// vertex gstart[g+1] - 1.  row_ptr is written for the block's own vertices
+// only (a spare's row end is never read).
 template <typename Off>
 __global__ void k_place(const Off* __restrict__ urp, const int* __restrict__ ucol, long long nu,
                         long long V0, long long E0, const long long* __restrict__ gstart,
@@ -96,24 +103,22 @@ __global__ void k_place(const Off* __restrict__ urp, const int* __restrict__ uco
                         int* __restrict__ slot_of, int* __restrict__ list, long long NV,
                         uint32_t* __restrict__ bm, SweepCtl* ctl, int cs) {
     const int lane = threadIdx.x & 31;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 <= nu;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < nu;
          i0 += (long long)gridDim.x * blockDim.x) {
         const long long i = i0 + threadIdx.x;
         int tier = -1;
-        long long v = V0 + i;
-        if (i <= nu) {
-            rp[v] = E0 + (long long)urp[i];
-            if (i < nu) {
-                const long long b = (long long)urp[i], e = (long long)urp[i + 1];
+        const long long v = V0 + i;
+        if (i < nu) {
+            const long long b = (long long)urp[i], e = (long long)urp[i + 1];
+            rp[v] = E0 + b;
+            const int g = slot_index(gstart, ng, i);
+            if (i + 1 < gstart[g + 1]) {  // a real vertex of graph g
                 for (long long j = b; j < e; j++) col[E0 + j] = (int)(V0 + ucol[j]);
                 const long long d = e - b;
-                const int g = slot_index(gstart, ng, i);
-                const bool real = i < gstart[g + 1];  // the spare vertex of a block is not
                 tier = d <= t_lo ? 0 : (d <= t_hi ? 1 : 2);
                 est[v] = ((uint32_t)tier << kEstBits) | (uint32_t)d;
-                slot_of[v] = real ? gslot[g] : -1;
-                if (!real) tier = -1;
-            } else {
+                slot_of[v] = gslot[g];
+            } else {                      // its spare vertex
                 est[v] = 0;
                 slot_of[v] = -1;
             }
@@ -150,14 +155,10 @@ __global__ void k_union(const int* __restrict__ raw, const long long* __restrict
     }
 }
 
-// starts[i] <- row_ptr[starts[i]] (in place: one thread per boundary).
-__global__ void k_gather_rp(const long long* __restrict__ urp, const long long* starts, int count,
-                            long long* out) {
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        const long long v = urp[starts[i]];
-        __syncwarp();
-        out[i] = v;
-    }
+// starts[i] <- row_ptr[starts[i]] (in place: each thread reads and writes
+// only its own boundaries).
+__global__ void k_gather_rp(const long long* __restrict__ urp, long long* starts, int count) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) starts[i] = urp[starts[i]];
 }
 
 // Per-slot count of the vertices in the current frontier.
@@ -214,7 +215,7 @@ struct kcore_batch {
     std::mutex step_mu;  // one engine step at a time
     // statistics
     long long submitted = 0, completed = 0, cancelled = 0, failed = 0, launches = 0, sweeps = 0,
-              admissions = 0;
+              admissions = 0, admitted_while_busy = 0;
     double busy_s = 0, admit_s = 0, sweep_s = 0, retire_s = 0;
     std::vector<double> latencies;
 };
@@ -335,7 +336,7 @@ kcore_status retire(kcore_batch* b) {
     const int cs = (int)(b->sweep % kSlots);
     cudaError_t e = cudaMemsetAsync(b->slot_cnt, 0, sizeof(int) * b->opt.max_slots, b->stream);
     if (e == cudaSuccess) {
-        k_slot_count<<<152 * 4, 256, 0, b->stream>>>(b->list[b->sweep % kParities], b->NV, b->ctl, cs,
+        k_slot_count<<<sm_count() * 4, 256, 0, b->stream>>>(b->list[b->sweep % kParities], b->NV, b->ctl, cs,
                                                      b->slot_of, b->slot_cnt);
         count_launch();
         e = cudaGetLastError();
@@ -391,6 +392,7 @@ kcore_status retire(kcore_batch* b) {
         b->resident--;
         r->state = Request::DONE;
         r->t_done = now_s();
+        r->retire_launch = b->launches;
         if (r->cancelled) {
             b->cancelled++;
         } else if (r->status == KCORE_OK) {
@@ -405,7 +407,12 @@ kcore_status retire(kcore_batch* b) {
 }
 
 // Admit queued graphs that fit.  Called with step_mu held, GPU idle.
-kcore_status admit(kcore_batch* b) {
+// A failure before placement (allocation, upload, cleaning) is confined to
+// the admission batch: its graphs fail, its ranges and slots are given back
+// and the resident graphs go on.  *fatal is set when the failure came during
+// or after placement into the arena, whose state is then not trusted.
+kcore_status admit(kcore_batch* b, bool* fatal) {
+    *fatal = false;
     std::vector<Request*> batch;
     long long vtot = 0, etot = 0, samples = 0;
     {
@@ -421,8 +428,8 @@ kcore_status admit(kcore_batch* b) {
                 b->cv_done.notify_all();
                 continue;
             }
-            const long long v = r->n, ee = 2LL * r->nnz;
-            if (vtot + v + 1 > vfree || etot + ee > efree) break;
+            const long long v = r->n + 1, ee = 2LL * r->nnz;  // with its spare vertex
+            if (vtot + v > vfree || etot + ee > efree) break;
             b->queue.pop_front();
             r->slot = b->free_slots.back();
             b->free_slots.pop_back();
@@ -433,8 +440,8 @@ kcore_status admit(kcore_batch* b) {
         }
     }
     if (batch.empty()) return KCORE_OK;
-    // the disjoint union of the batch, one spare vertex at the end
-    const long long nu = vtot + 1;
+    // the disjoint union of the batch, each graph followed by its spare vertex
+    const long long nu = vtot;
     const int nb = (int)batch.size();
     std::vector<long long> gstart(nb + 1), sstart(nb + 1);
     std::vector<int> gslot(nb);
@@ -444,7 +451,7 @@ kcore_status admit(kcore_batch* b) {
         sstart[i] = so;
         gslot[i] = batch[i]->slot;
         so += batch[i]->nnz;
-        vo += batch[i]->n;
+        vo += batch[i]->n + 1;
     }
     gstart[nb] = vo;
     sstart[nb] = so;
@@ -486,7 +493,7 @@ kcore_status admit(kcore_batch* b) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dsl, gslot.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && samples) {
-        const int g = (int)std::min<long long>((samples + 255) / 256, 152LL * 8);
+        const int g = (int)std::min<long long>((samples + 255) / 256, (long long)sm_count() * 8);
         k_union<<<g, 256, 0, st>>>(raw, dss, dgs, nb, samples, dsrc, dst_);
         count_launch();
         e = cudaGetLastError();
@@ -511,16 +518,17 @@ kcore_status admit(kcore_batch* b) {
         if (V0 < 0 || E0 < 0) s = fail(KCORE_ERR_OOM, "batch arena fragmented");
     }
     if (s == KCORE_OK) {
+        *fatal = true;  // placement writes into the arena's frontier
         const int cs = (int)(b->sweep % kSlots), pc = (int)(b->sweep % kParities);
-        const int g = (int)std::min<long long>((nu + 256) / 256, 152LL * 16);
+        const int g = (int)std::min<long long>((nu + 256) / 256, (long long)sm_count() * 16);
         k_place<long long><<<g, 256, 0, st>>>(
-            (const long long*)csr.row_ptr, csr.col, nu - 1, V0, E0, dgs, dsl, nb,
+            (const long long*)csr.row_ptr, csr.col, nu, V0, E0, dgs, dsl, nb,
             b->opt.sweep.t_lo, b->opt.sweep.t_hi, b->rp, b->col, b->est, b->slot_of, b->list[pc],
             b->NV, b->bitmap[pc], b->ctl, cs);
         count_launch();
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            k_gather_rp<<<1, 256, 0, st>>>((const long long*)csr.row_ptr, dgs, (int)gstart.size(), dgs);
+            k_gather_rp<<<1, 256, 0, st>>>((const long long*)csr.row_ptr, dgs, (int)gstart.size());
             count_launch();
             e = cudaGetLastError();
         }
@@ -529,13 +537,14 @@ kcore_status admit(kcore_batch* b) {
                                 cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_status(e, "batch placement");
+        else *fatal = false;
     }
-    cudaFreeAsync(raw, st);
-    cudaFreeAsync(dsrc, st);
-    cudaFreeAsync(dst_, st);
-    cudaFreeAsync(dgs, st);
-    cudaFreeAsync(dss, st);
-    cudaFreeAsync(dsl, st);
+    dfree(raw, st);
+    dfree(dsrc, st);
+    dfree(dst_, st);
+    dfree(dgs, st);
+    dfree(dss, st);
+    dfree(dsl, st);
     dfree(csr.row_ptr, st);
     dfree(csr.col, st);
     cudaStreamSynchronize(st);  // no upload from the samples' storage in flight
@@ -555,12 +564,18 @@ kcore_status admit(kcore_batch* b) {
         return s;
     }
     b->admissions++;
-    // per-graph ranges inside the block; the spare vertex and the block's
-    // unused entry slack go with the last graph
+    // per-graph ranges inside the block: each graph with its spare vertex;
+    // the block's unused entry slack goes with the last graph
+    const double t_admit = now_s();
+    const int before = b->resident;
+    if (before > 0) b->admitted_while_busy += (long long)batch.size();
     for (size_t i = 0; i < batch.size(); i++) {
         Request* r = batch[i];
+        r->t_admit = t_admit;
+        r->admit_launch = b->launches;
+        r->resident_at_admit = before;
         r->v0 = V0 + gstart[i];
-        r->vlen = r->n + (i + 1 == batch.size() ? 1 : 0);
+        r->vlen = r->n + 1;
         r->e0 = E0 + bound[i];
         r->elen = (i + 1 == batch.size() ? std::max<long long>(csr.nnz, 1) : bound[i + 1]) - bound[i];
         r->state = Request::RESIDENT;
@@ -626,7 +641,9 @@ kcore_status step(kcore_batch* b, int64_t* active) {
     std::lock_guard<std::mutex> sl(b->step_mu);
     cudaSetDevice(b->device);
     const double t0 = now_s();
-    kcore_status s = admit(b);
+    bool fatal = false;
+    const kcore_status sa = admit(b, &fatal);  // a confined failure is on its tickets
+    kcore_status s = fatal ? sa : KCORE_OK;
     const double t1 = now_s();
     bool any;
     {
@@ -794,7 +811,8 @@ kcore_status kcore_batch_create(const kcore_serve_options* opt, kcore_batch** ou
     if (o.host_staging > 0) {
         // the pool is an optimisation: without it copies use pageable memory
         const long long words = o.host_staging / (long long)sizeof(int32_t);
-        if (cudaHostAlloc((void**)&b->hpool, sizeof(int32_t) * words, cudaHostAllocDefault) == cudaSuccess) {
+        if (!alloc_fault() &&
+            cudaHostAlloc((void**)&b->hpool, sizeof(int32_t) * words, cudaHostAllocDefault) == cudaSuccess) {
             b->hr.reset(words);
         } else {
             b->hpool = nullptr;
@@ -856,6 +874,11 @@ kcore_status kcore_submit(kcore_batch* b, int64_t n, const void* row_ptr, int32_
 }
 
 kcore_status kcore_poll(kcore_batch* b, uint64_t ticket, int32_t* coreness_out, int64_t timeout_us) {
+    return kcore_poll_info(b, ticket, coreness_out, timeout_us, nullptr);
+}
+
+kcore_status kcore_poll_info(kcore_batch* b, uint64_t ticket, int32_t* coreness_out,
+                             int64_t timeout_us, kcore_ticket_info* info) {
     if (!b) return fail(KCORE_ERR_INVALID, "NULL batch");
     std::unique_lock<std::mutex> lk(b->mu);
     auto it = b->reqs.find(ticket);
@@ -884,6 +907,14 @@ kcore_status kcore_poll(kcore_batch* b, uint64_t ticket, int32_t* coreness_out, 
         if (!ready()) return KCORE_PENDING;
     }
     kcore_status s = r->cancelled ? KCORE_ERR_CANCELLED : r->status;
+    if (info) {
+        info->submit_s = r->t_submit;
+        info->admit_s = r->t_admit;
+        info->done_s = r->t_done;
+        info->admit_launch = r->admit_launch;
+        info->retire_launch = r->retire_launch;
+        info->resident_at_admit = r->resident_at_admit;
+    }
     if (s == KCORE_OK && coreness_out && r->n) {
         const uint32_t* raw = r->res;
         for (int64_t i = 0; i < r->n; i++) coreness_out[i] = (int32_t)(raw[i] & kEstMask);
@@ -931,6 +962,7 @@ kcore_status kcore_batch_stats_get(kcore_batch* b, kcore_batch_stats* out) {
     out->sweep_s = b->sweep_s;
     out->retire_s = b->retire_s;
     out->admissions = b->admissions;
+    out->admitted_while_busy = b->admitted_while_busy;
     if (!b->latencies.empty()) {
         std::vector<double> l = b->latencies;
         std::sort(l.begin(), l.end());

@@ -86,6 +86,8 @@ struct Acc {
     unsigned long long degsum;   // frontier degree sum
     unsigned long long skipped;  // adjacency entries an early exit did not read
     unsigned long long dec;      // sum of estimate decreases
+    unsigned long long deg_w;    // of which warp tier
+    unsigned long long deg_c;    // of which CTA tier
 };
 
 // Per-warp push buffers: each warp collects its pushes in its own slice of
@@ -527,6 +529,7 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
     if (lane == 0) {
         acc.evaluated += 1;
         acc.degsum += (unsigned)d;
+        acc.deg_w += (unsigned)d;
     }
     if (k == 0) {
         if (S.mark && lane == 0) mark_done(S, u);
@@ -594,6 +597,7 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
     if (lane == 0) {
         acc.evaluated += 1;
         acc.degsum += (unsigned)d;
+        acc.deg_w += (unsigned)d;
     }
     if (k == 0) {
         if (S.mark && lane == 0) mark_done(S, u);
@@ -820,6 +824,7 @@ __device__ __forceinline__ void hub_vertex(const Sweep& S, WarpQ& Q, const Off* 
     if (tid == 0) {
         acc.evaluated += 1;
         acc.degsum += (unsigned long long)d;
+        acc.deg_c += (unsigned long long)d;
     }
     if (k == 0) {
         if (S.mark && tid == 0) mark_done(S, u);
@@ -1031,7 +1036,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
     bool prev_tail = tail;
     unsigned my_epoch = 0;
     unsigned nbar = 0;
-    unsigned long long tot[kAccN] = {0, 0, 0, 0, 0, 0};  // block 0, thread 0: run totals
+    unsigned long long tot[kAccN] = {};  // block 0, thread 0: run totals
     long long tail_sweeps = 0;
     long long s = a.first_sweep;
     if (tid == 0) {
@@ -1074,7 +1079,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
             const unsigned f2 = __ldcg(&ctl->fcnt[cur][2]);
             const int st = __ldcg(&ctl->status);
             unsigned pv[kTiers] = {0u, 0u, 0u};
-            unsigned long long av[kAccN] = {0, 0, 0, 0, 0, 0};
+            unsigned long long av[kAccN] = {};
             if (s > 0)
                 for (int q = 0; q < kTiers; q++) pv[q] = __ldcg(&ctl->fcnt[prv][q]);
             const bool book = blockIdx.x == 0 && s > a.first_sweep;
@@ -1097,11 +1102,19 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                     tr[kTrUpdates] = (long long)av[kAccUpdates];
                     tr[kTrRead] = (long long)(av[kAccDegsum] - av[kAccSkipped]);
                     tr[kTrDec] = (long long)av[kAccDec];
+                    tr[kTrDegW] = (long long)av[kAccDegW];
+                    tr[kTrDegC] = (long long)av[kAccDegC];
                 }
                 if (prev_tail) tail_sweeps += 1;
             }
             // start time of sweep s (globaltimer, ns)
-            if (blockIdx.x == 0 && s < a.max_trace) a.trace[s * kTraceCols + kTrStart] = (long long)gtime_ns();
+            if (blockIdx.x == 0 && s < a.max_trace) {
+                long long* tr = a.trace + s * kTraceCols;
+                tr[kTrStart] = (long long)gtime_ns();
+                tr[kTrF0] = f0;
+                tr[kTrF1] = f1;
+                tr[kTrF2] = f2;
+            }
             // slot of sweep s-2: free now, push target of sweep s+1
             if (blockIdx.x == 0) {
                 const int old = (int)((s + 2) % kSlots);
@@ -1203,7 +1216,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
         S.bmn = a.bitmap[p_nxt];
         S.wbuf = s_wbuf + wid * kWCap;
         WarpQ Q = {{0u, 0u, 0u}};
-        Acc acc = {0u, 0u, 0u, 0ull, 0ull, 0ull};
+        Acc acc = {0u, 0u, 0u, 0ull, 0ull, 0ull, 0ull, 0ull};
         const unsigned warps_all = (tail ? 1u : gridDim.x) * (unsigned)nwarps;
         const long long gthreads = tail ? blockDim.x : (long long)gridDim.x * blockDim.x;
         const long long gt = tail ? tid : (long long)blockIdx.x * blockDim.x + tid;
@@ -1322,8 +1335,8 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
 
         // ---- per-sweep statistics
         {
-            unsigned long long v4[kAccN] = {acc.evaluated, acc.degsum, acc.updates,
-                                            acc.pushes,    acc.skipped, acc.dec};
+            unsigned long long v4[kAccN] = {acc.evaluated, acc.degsum, acc.updates, acc.pushes,
+                                            acc.skipped,   acc.dec,    acc.deg_w,   acc.deg_c};
 #pragma unroll
             for (int i = 0; i < kAccN; i++) {
                 unsigned long long x = v4[i];
@@ -1458,7 +1471,7 @@ __global__ void k_warm_init(const Off* __restrict__ rp, const int* __restrict__ 
 cudaError_t launch_warm_init(const SweepArgs& a, const void* row_ptr, const uint32_t* est0,
                              const int* start, const int* frontier, long long nf, cudaStream_t st) {
     const long long items = std::max<long long>({(long long)a.n, nf, 1LL});
-    const int g = (int)std::min<long long>((items + 255) / 256, 152LL * 32);
+    const int g = (int)std::min<long long>((items + 255) / 256, (long long)sm_count() * 32);
     if (a.off64)
         k_warm_init<<<g, 256, 0, st>>>((const long long*)row_ptr, a.col, a.n, est0, start, a.est,
                                       frontier, nf, a.bitmap[0], a.list[0], a.tier_off[0],

@@ -121,3 +121,93 @@ def test_admission_errors_and_cancel():
         assert st == K.KCORE_ERR_CANCELLED
         with pytest.raises(K.KCoreError):
             eng.submit_coo(5, np.array([0, 7], np.int32), np.array([1, 1], np.int32))
+
+
+def stream_range_indices():
+    """Indices of the 20,000-graph stream (n log-uniform in [100, 200000],
+    ER / R-MAT / damaged grid) covering its whole range: the three largest and
+    the two smallest graphs of each family, and the first 30 of the stream."""
+    params = [graphgen.stream_params(i) for i in range(20000)]
+    pick = list(range(30))
+    for fam in graphgen.STREAM_FAMILIES:
+        by_n = sorted((n, i) for i, (n, f) in enumerate(params) if f == fam)
+        pick += [i for _, i in by_n[-3:]] + [i for _, i in by_n[:2]]
+    return sorted(set(pick)), params
+
+
+def test_stream_full_range_in_waves_matches_oracle_and_overlaps():
+    """Graphs from the whole size range of the stream (up to n = 199,809, all
+    three families) submitted in waves while earlier ones are resident, into
+    an arena that holds several of the largest at once.  Every result must
+    equal the oracle's coreness (the unique fixed point of the iteration,
+    Alg. 1), and the engine must have placed graphs while others were still
+    resident and unfinished: for some pair, B's first launch lies inside A's
+    launches."""
+    idx, params = stream_range_indices()
+    assert max(params[i][0] for i in idx) > 199_000
+    assert {params[i][1] for i in idx} == set(graphgen.STREAM_FAMILIES)
+    graphs = [graphgen.stream_graph(i) for i in idx]
+    opts = K.default_serve_options(mem_budget=96 << 20, chunk_sweeps=2)
+    waves = [graphs[j::3] for j in range(3)]
+    infos, results = [], []
+    with K.BatchEngine(opts) as eng:
+        tickets = []
+        for w, wave in enumerate(waves):
+            for g in wave:
+                tickets.append((g, eng.submit_coo(g.n, g.src, g.dst)))
+            if w + 1 < len(waves):          # the next wave arrives while this one runs
+                t_end = time.perf_counter() + 5.0
+                while eng.stats()["launches"] < 2 * (w + 1) and time.perf_counter() < t_end:
+                    time.sleep(0.0005)
+        for g, t in tickets:
+            st, core, info = eng.poll_info(t, g.n, timeout_us=-1)
+            assert st == K.KCORE_OK, K.lib().kcore_last_error()
+            results.append((g, core))
+            infos.append(info)
+        s = eng.stats()
+    for g, core in results:
+        np.testing.assert_array_equal(core, oracle_core(g), err_msg=g.name)
+    assert s["completed"] == len(graphs) and s["failed"] == 0
+    assert s["admitted_while_busy"] > 0
+    overlap = any(a["admit_launch"] < b["admit_launch"] < a["retire_launch"]
+                  for a in infos for b in infos)
+    assert overlap, "no graph was admitted while another was resident and unfinished"
+    for info in infos:
+        assert info["submit_s"] <= info["admit_s"] <= info["done_s"]
+        assert 0 <= info["admit_launch"] < info["retire_launch"]
+
+
+def test_freed_neighbour_range_reused_while_a_graph_is_resident():
+    """Graphs admitted together sit next to each other in the arena.  Here a
+    tiny graph H retires while its block neighbour G (a long path, which
+    converges over many sweeps, with its middle vertex numbered last) is still
+    resident, and a new graph X is placed into H's freed range.  G's last
+    row must be unaffected: every result equals the oracle's coreness."""
+    L = 4001
+    order = list(range(L - 1))
+    order.insert(L // 2, L - 1)                       # vertex L-1 in the middle of the path
+    g_src = np.array(order[:-1], np.int32)
+    g_dst = np.array(order[1:], np.int32)
+    G = graphgen.EdgeList(L, g_src, g_dst, "path_middle_last")
+    H = graphgen.EdgeList(3, np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32), "triangle")
+    X = graphgen.EdgeList(2, np.array([0], np.int32), np.array([1], np.int32), "edge")
+    opts = K.default_serve_options(mem_budget=32 << 20, start_thread=0, chunk_sweeps=1)
+    with K.BatchEngine(opts) as eng:
+        tg = eng.submit_coo(G.n, G.src, G.dst)
+        th = eng.submit_coo(H.n, H.src, H.dst)          # same admission, right after G
+        eng.step()
+        steps = 1
+        while eng.poll(th, H.n, timeout_us=0)[0] == K.KCORE_PENDING:
+            eng.step()
+            steps += 1
+            assert steps < 100
+        assert eng.stats()["resident"] == 1              # G is still running
+        tx = eng.submit_coo(X.n, X.src, X.dst)           # fits into H's freed range
+        while eng.step() > 0:
+            steps += 1
+            assert steps < 100000
+        for g, t in ((G, tg), (X, tx)):
+            st, core, info = eng.poll_info(t, g.n, timeout_us=0)
+            assert st == K.KCORE_OK
+            np.testing.assert_array_equal(core, oracle_core(g), err_msg=g.name)
+        assert info["resident_at_admit"] == 1
