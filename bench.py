@@ -1,21 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the k-core hot path on GB300; prints ONE JSON line.
 
-A step is one pass of the whole path over one synthetic graph whose raw edge
-samples are already resident in HBM: device CSR cleaning (kcore_create_coo),
-estimate initialisation, the persistent sweep kernel until the frontier is
-empty, and the int32 coreness written to a device buffer (kcore_run).
-value = undirected edges m of the cleaned graph per second of step time.
+Default workload: the social-graph stand-in, R-MAT scale 24 with edge factor
+32 and (a, b, c) = (0.45, 0.22, 0.22), symmetrised and deduplicated, plus a
+planted G(5000, 0.5) core (n = 16,777,216, m = 542,922,765; int64 row_ptr);
+the sweep knobs are picked by the library's autotuner first and every run is
+a replayed CUDA graph.  A step is one pass of the whole path over the graph
+whose raw edge samples are already resident in HBM: device CSR cleaning
+(kcore_create_coo), estimate initialisation, the persistent sweep kernel until
+the frontier is empty, and the int32 coreness written to a device buffer
+(kcore_run).  value = undirected edges m of the cleaned graph per second of
+step time.
 
 Also reported: the same metric end to end through the C ABI with host
 buffers (pinned host -> device copy of the samples and device -> host copy of
 the coreness inside the timed region), the decomposition alone on the
 resident graph (the paper's timing: load excluded, setup included), the sweep
 kernel's roofline fraction against the measured HBM copy bandwidth, the
-oracle on the host cores, and SM clocks sampled during the timed region.
+oracle's Batagelj-Zaversnik peel of the whole graph on one host core (its
+host CSR build timed apart), SM clocks sampled during the timed region, and
+`stream`: the batching / serving workload (20,000 graphs, n log-uniform in
+[100, 200000], ER / R-MAT / damaged grid) as batched graphs/s and p50/p99
+latency of the continuous-batching engine against one create + run per
+graph, both served for real under the same Poisson arrivals, every result
+compared with the oracle.
 
---impl reference times the oracle (plain C Batagelj-Zaversnik plus its host
-CSR build) on the host cores on the same workload and metric.
+--impl reference times the oracle (plain C Batagelj-Zaversnik over its own
+host CSR) on the host cores on the same workload and metric.
 
 Launch: python bench.py [--gpus 1] [--steps K] [--warmup W] [--workload NAME];
 for N > 1 under torch.distributed.run, each rank decomposes its own copy of
@@ -48,19 +59,35 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="road2048")
+    ap.add_argument("--workload", default="rmat24_planted",
+                    help="er10k | road2048 | rmat22 | rmat24_planted | stream (the stream alone)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
-    ap.add_argument("--stream-count", type=int, default=1000)
-    ap.add_argument("--host-staging-gib", type=int, default=4,
-                    help="page-locked host staging of the batch engine (stream workload)")
-    ap.add_argument("--arena-gib", type=int, default=8)
+    ap.add_argument("--cpu-budget-s", type=float, default=30.0,
+                    help="oracle time the CPU baseline may take per timed pass (whole graph "
+                         "when one peel fits; else a prefix of the samples)")
+    ap.add_argument("--ref-budget-s", type=float, default=100.0,
+                    help="reference arm: timed oracle peels are capped to fit this budget")
+    ap.add_argument("--stream-count", type=int, default=20000)
+    ap.add_argument("--no-stream", action="store_true", help="skip the batching / serving stream")
+    ap.add_argument("--host-staging-gib", type=int, default=8,
+                    help="page-locked host staging of the batch engine (stream)")
+    ap.add_argument("--arena-gib", type=int, default=16)
     ap.add_argument("--chunk-sweeps", type=int, default=16)
-    ap.add_argument("--autotune", action="store_true",
-                    help="tune the sweep knobs on the workload first (paper_2512_00233_gb300.autotune)")
-    ap.add_argument("--graph", action="store_true",
-                    help="decomposition-only runs replay a captured CUDA graph (KCORE_GRAPH)")
-    return ap.parse_args()
+    ap.add_argument("--check-workers", type=int, default=12,
+                    help="oracle processes that check every stream result")
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=None,
+                    help="tune the sweep knobs on the workload first (default for rmat24_planted)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--graph", dest="graph", action="store_true", default=None,
+                    help="runs replay a captured CUDA graph (KCORE_GRAPH; default for rmat24_planted)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
+    a = ap.parse_args()
+    heavy = a.workload == "rmat24_planted"
+    if a.autotune is None:
+        a.autotune = heavy
+    if a.graph is None:
+        a.graph = heavy
+    return a
 
 
 def dist_env():
@@ -216,73 +243,94 @@ def combine_ranks(local_ms: float, units_per_rank: float, steps: int, device=Non
 
 
 # ---------------------------------------------------------------- oracle on the host
-def oracle_pass(g):
+def oracle_peel_baseline(workload: str, budget_s: float, omp_threads: int = 4) -> dict:
+    """The oracle on the whole workload, in a process of its own: its host CSR
+    build, then Batagelj-Zaversnik peels (single thread), each timed; as many
+    peels (1..5) as fit the budget after the first.  Generation of the samples
+    (OpenMP, `omp_threads`) is not timed."""
+    os.environ["OMP_NUM_THREADS"] = str(omp_threads)   # before graphgen's library loads
+    import graphgen
     import oracle
+    g = graphgen.workload(workload)
+    n, samples = g.n, g.samples
     t0 = time.perf_counter()
     rp, col = oracle.csr_build(g.n, g.src, g.dst)
-    core = oracle.coreness(g.n, rp, col)
-    dt = time.perf_counter() - t0
-    return dt, int(rp[-1]) // 2, core
-
-
-def oracle_sample(g, budget_s: float):
-    """The workload itself if one oracle pass fits the budget, else a prefix of
-    its samples sized to fit (same vertex set).  Workloads up to 20 M samples
-    run whole (road2048: about 0.3 s per pass); larger ones are sized from a
-    4 M-sample prefix."""
-    import graphgen
-    if g.samples <= 20_000_000:
-        return g, "full workload"
-    k0 = 4_000_000
-    dt, _, _ = oracle_pass(graphgen.EdgeList(g.n, g.src[:k0], g.dst[:k0]))
-    k = max(k0, min(g.samples, int(budget_s / max(dt, 1e-6) * k0)))
-    if k >= g.samples:
-        return g, "full workload"
-    return (graphgen.EdgeList(g.n, g.src[:k], g.dst[:k]),
-            f"first {k} of {g.samples} edge samples (same vertex set)")
-
-
-def cpu_baseline(g, budget_s: float):
-    sample, desc = oracle_sample(g, budget_s / 2)
-    times, m = [], 0
-    t_start = time.perf_counter()
+    csr_s = time.perf_counter() - t0
+    del g
+    peels = []
     while True:
-        dt, m, _ = oracle_pass(sample)
-        times.append(dt)
-        if time.perf_counter() - t_start > budget_s / 2 or len(times) >= 5:
+        t0 = time.perf_counter()
+        core = oracle.coreness(n, rp, col)
+        peels.append(time.perf_counter() - t0)
+        if len(peels) >= 5 or sum(peels) + peels[0] > budget_s:
             break
-    v = m / statistics.mean(times)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{desc}; {len(times)} pass(es) of host CSR build + Batagelj-Zaversnik, "
-                      f"single thread, mean {statistics.mean(times):.3f} s per pass"}
+    return {"n": n, "samples": samples, "m": int(rp[-1]) // 2, "csr_s": csr_s, "peels": peels,
+            "kmax": int(core.max()) if n else 0}
+
+
+def cpu_baseline_line(r: dict) -> dict:
+    mean = statistics.mean(r["peels"])
+    return {"value": r["m"] / mean, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"whole workload (n {r['n']}, m {r['m']}): {len(r['peels'])} "
+                      f"Batagelj-Zaversnik peel(s) of the oracle's own host CSR, single thread, "
+                      f"mean {mean:.3f} s; the oracle's host CSR build took {r['csr_s']:.1f} s "
+                      f"(reported apart, not in the value)",
+            "peel_s": r["peels"], "csr_build_s": r["csr_s"]}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: the whole workload's host CSR
+    built once (timed, reported apart), then timed peels.  One peel of the
+    largest workload takes tens of seconds, so the timed peels are capped to
+    fit --ref-budget-s (at least one); the line states the count."""
     import graphgen
+    import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     g = graphgen.workload(args.workload)
-    sample, desc = oracle_sample(g, 3.0)
-    for _ in range(args.warmup):
-        oracle_pass(sample)
-    times, m = [], 0
-    for _ in range(args.steps):
-        dt, m, _ = oracle_pass(sample)
-        times.append(dt)
+    name, n, samples = g.name, g.n, g.samples
+    t0 = time.perf_counter()
+    rp, col = oracle.csr_build(g.n, g.src, g.dst)
+    csr_s = time.perf_counter() - t0
+    del g
+    m = int(rp[-1]) // 2
+    warm = min(args.warmup, 1)
+    t_est = None
+    for _ in range(warm):
+        t0 = time.perf_counter()
+        oracle.coreness(n, rp, col)
+        t_est = time.perf_counter() - t0
+    times = []
+    while len(times) < args.steps:
+        t0 = time.perf_counter()
+        oracle.coreness(n, rp, col)
+        times.append(time.perf_counter() - t0)
+        t_est = t_est or times[0]
+        if len(times) >= max(1, int(args.ref_budget_s // t_est)):
+            break
     total = sum(times)
-    value = m * args.steps / total
+    value = m * len(times) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps, "warmup": warm,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": g.name, "n": g.n, "samples": g.samples, "m": m},
+        "config": workload_config(name, n, samples, m),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{desc}; host CSR build + Batagelj-Zaversnik per step"},
+                         "sample": f"whole workload; {len(times)} timed Batagelj-Zaversnik peel(s) "
+                                   f"of the oracle's own host CSR (built once in {csr_s:.1f} s, "
+                                   f"not timed), single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "csr_build_s": csr_s,
     }
     print(json.dumps(line), flush=True)
+
+
+def workload_config(name, n, samples, m) -> dict:
+    """The `config` object, the same for both arms."""
+    return {"workload": name, "n": n, "samples": samples, "m": m,
+            "l2": "512 MiB buffer rewritten between timed steps"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -294,6 +342,18 @@ def run_ours(args):
     import paper_2512_00233_gb300 as K
 
     ws, rank, local = dist_env()
+    # the oracle's CPU baseline runs in a spawned process of its own once the
+    # timed GPU work is over (its host CSR build would compete with the host
+    # copies of the timed regions), beside the stream's result check
+    cpu = {}
+
+    def start_cpu_baseline():
+        if ws == 1 and not args.no_cpu_baseline and not cpu:
+            import multiprocessing as mp
+            from concurrent.futures import ProcessPoolExecutor
+            cpu["pool"] = ProcessPoolExecutor(1, mp_context=mp.get_context("spawn"))
+            cpu["job"] = cpu["pool"].submit(oracle_peel_baseline, args.workload, args.cpu_budget_s)
+
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -320,15 +380,18 @@ def run_ours(args):
 
     opts = None
     tuned = None
+    t_tune = 0.0
     if args.autotune:
         from paper_2512_00233_gb300 import autotune
+        t0 = time.perf_counter()
         with K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes) as gt:
             opts, _ = autotune.autotune(gt, reps=2, passes=1, cache=None)
+        t_tune = time.perf_counter() - t0
         tuned = {k: getattr(opts, k) for k in autotune.SPACE}
 
     def step_device():
         g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes, options=opts)
-        g.run(out=out_d)
+        g.run(out=out_d, graph=args.graph)
         return g
 
     # warm-up (also gives m and the per-run statistics)
@@ -395,6 +458,7 @@ def run_ours(args):
         if i >= args.warmup:
             e2e_t.append(t1 - t0)
     e2e_value = m * ws / statistics.mean(e2e_t)
+    del src_h, dst_h, src_d, dst_d
 
     # ---- roofline of the sweep kernel (dominant kernel of the decomposition)
     peak, peak_kind = measured_peaks()
@@ -411,16 +475,20 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": local_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": g0.name, "n": g0.n, "samples": g0.samples, "m": m,
-                       "row_ptr_bytes": rp_bytes, "l2": "512 MiB buffer rewritten between steps",
-                       "step": "kcore_create_coo (device samples) + kcore_run (device output)",
-                       "options": tuned or "library defaults"},
+            "config": workload_config(g0.name, g0.n, g0.samples, m),
+            "setup": {"row_ptr_bytes": rp_bytes,
+                      "step": "kcore_create_coo (device samples) + kcore_run (device output"
+                              + (", replayed CUDA graph)" if args.graph else ")"),
+                      "inputs_vs_l2": f"{8 * g0.samples / 2**30:.2f} GiB of samples against a "
+                                      "129 MB L2",
+                      "options": tuned or "library defaults",
+                      "autotune_s": t_tune},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * g0.samples,
                     "d2h_bytes_per_step": 4 * g0.n},
             "gpu_launches": launches,
+            "create_ms": create_ms,
             "decompose": {"value": m / (statistics.mean(run_ms) / 1e3), "unit": UNIT,
                           "ms_run": statistics.mean(run_ms), "ms_sweep": sweep_ms,
-                          "ms_create": create_ms,
                           "sweeps": statistics.mean(s["sweeps"] for s in sweep_stats),
                           "tail_sweeps": statistics.mean(s["tail_sweeps"] for s in sweep_stats),
                           "evaluated": statistics.mean(s["evaluated"] for s in sweep_stats),
@@ -434,8 +502,14 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "wall_s": t_wall,
         }
-        if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(g0, args.cpu_budget_s)
+    del g0
+    if rank == 0 and ws == 1 and not args.no_stream:
+        line["stream"] = run_stream(args, K, torch, after_timed=start_cpu_baseline)
+    start_cpu_baseline()
+    if line is not None and cpu:
+        line["cpu_baseline"] = cpu_baseline_line(cpu["job"].result())
+        cpu["pool"].shutdown()
+    if line is not None:
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -443,121 +517,215 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- batched / served stream
-def run_stream(args):
-    """The batch/serving workload: a stream of graphs with vertex counts
-    log-uniform in [100, 200000] (ER avg degree 8, R-MAT edge factor 8, damaged
-    grid), bounded to --stream-count graphs.  Measures
-      - one launch per graph: kcore_create_coo + kcore_run per graph, in order;
-      - batched, saturated: every graph submitted at once to the engine;
-      - served: Poisson arrivals at 0.7 x the saturated batched rate, p50/p99
-        latency from submission to result (engine clock); the one-launch-per-
-        graph server's p50/p99 at the same arrivals follow from its measured
-        per-graph service times (single FIFO server)."""
+def result_hash(core) -> bytes:
     import numpy as np
-    import torch
+    return hashlib.blake2b(np.ascontiguousarray(core, dtype=np.int32).tobytes(),
+                           digest_size=16).digest()
+
+
+def oracle_stream_hashes(lo: int, hi: int) -> list:
+    """Oracle coreness hashes of stream graphs [lo, hi) (a spawned worker)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import graphgen
+    import oracle
+    out = []
+    for i in range(lo, hi):
+        g = graphgen.stream_graph(i)
+        rp, col = oracle.csr_build(g.n, g.src, g.dst)
+        out.append((i, result_hash(oracle.coreness(g.n, rp, col)), int(rp[-1]) // 2))
+    return out
+
+
+def percentiles_ms(lat_s):
+    import numpy as np
+    a = np.asarray(lat_s) * 1e3
+    return float(np.percentile(a, 50)), float(np.percentile(a, 99))
+
+
+def serve_one_launch(K, graphs, arrivals):
+    """One kcore_create_coo + kcore_run (host samples in, host coreness out) per
+    request, by one server thread in arrival order.  `arrivals` None: every
+    request at once.  Latency = result in the caller's buffer - arrival
+    (time.perf_counter, CLOCK_MONOTONIC)."""
+    import queue
+
+    import numpy as np
+    G = len(graphs)
+    lat = np.zeros(G)
+    res = [None] * G
+    q = queue.SimpleQueue()
+
+    def server():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            i, t_arr = item
+            g = graphs[i]
+            with K.Graph.from_coo(g.n, g.src, g.dst) as gg:
+                res[i] = gg.run(device=False)
+            lat[i] = time.perf_counter() - t_arr
+
+    th = threading.Thread(target=server, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(G):
+        if arrivals is not None:
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+        q.put((i, time.perf_counter()))
+    q.put(None)
+    th.join()
+    return time.perf_counter() - t0, lat, res
+
+
+def serve_batched(K, opts, graphs, arrivals):
+    """The continuous-batching engine under the same arrivals: requests are
+    submitted at their arrival times while a poller thread collects results.
+    Latency = the engine's result-ready time (kcore_poll_info done_s, the same
+    monotonic clock) - arrival."""
+    import queue
+
+    import numpy as np
+    G = len(graphs)
+    t_arr = np.zeros(G)
+    lat = np.zeros(G)
+    res = [None] * G
+    infos = [None] * G
+    q = queue.SimpleQueue()
+    clock_ok = [True]
+    errors = []
+    with K.BatchEngine(opts) as eng:
+        for g in graphs[:3]:                       # warm-up
+            eng.poll(eng.submit_coo(g.n, g.src, g.dst), g.n, timeout_us=-1)
+
+        def poller():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                i, t = item
+                st, core, info = eng.poll_info(t, graphs[i].n, timeout_us=-1)
+                if st != K.KCORE_OK:
+                    errors.append(f"stream graph {i}: status {st}")
+                    continue
+                res[i], infos[i] = core, info
+                lat[i] = info["done_s"] - t_arr[i]
+                if not (t_arr[i] <= info["submit_s"] <= info["done_s"]):
+                    clock_ok[0] = False
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(G):
+            if arrivals is not None:
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            g = graphs[i]
+            t_arr[i] = time.perf_counter()
+            q.put((i, eng.submit_coo(g.n, g.src, g.dst)))
+        q.put(None)
+        th.join()
+        wall = time.perf_counter() - t0
+        stats = eng.stats()
+    if errors:
+        raise RuntimeError("; ".join(errors[:5]))
+    if not clock_ok[0]:
+        raise RuntimeError("engine times are not on the clock of time.perf_counter")
+    overlap = sum(1 for x in infos if x["resident_at_admit"] > 0)
+    return wall, lat, res, stats, overlap
+
+
+def run_stream(args, K, torch, after_timed=None):
+    """The batching / serving workload: the first --stream-count graphs of the
+    stream (n log-uniform in [100, 200000]; ER avg degree 8, R-MAT 8n samples,
+    damaged grid), host samples.  Both servers run for real, one after the
+    other on this GPU: saturated (every request at once) and under Poisson
+    arrivals at 0.7 x each server's saturated rate; every result of every run
+    is compared with the oracle's coreness afterwards (spawned processes)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor, ThreadPoolExecutor
 
     import graphgen
-    import paper_2512_00233_gb300 as K
-
-    torch.cuda.set_device(0)
     G = args.stream_count
-    graphs = [graphgen.stream_graph(i) for i in range(G)]
-    m_total = 0
-    # one launch per graph (warm-up on the first few)
-    for g in graphs[:3]:
-        with K.Graph.from_coo(g.n, g.src, g.dst) as gg:
-            gg.run(device=False)
-    service = []
+    graphgen.stream_params(0)                        # loads the generator before the threads
     t0 = time.perf_counter()
-    for g in graphs:
-        a = time.perf_counter()
-        with K.Graph.from_coo(g.n, g.src, g.dst) as gg:
-            gg.run(device=False)
-            m_total += gg.nnz // 2
-        service.append(time.perf_counter() - a)
-    t_one = time.perf_counter() - t0
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 4)) as ex:
+        graphs = list(ex.map(graphgen.stream_graph, range(G)))
+    t_gen = time.perf_counter() - t0
     opts = K.default_serve_options(mem_budget=args.arena_gib << 30, chunk_sweeps=args.chunk_sweeps,
                                    host_staging=args.host_staging_gib << 30)
-    # batched, saturated
-    with K.BatchEngine(opts) as eng:
-        for g in graphs[:3]:
-            eng.poll(eng.submit_coo(g.n, g.src, g.dst), g.n, timeout_us=-1)
-        t0 = time.perf_counter()
-        tickets = [eng.submit_coo(g.n, g.src, g.dst) for g in graphs]
-        t_submit = time.perf_counter() - t0
-        for g, t in zip(graphs, tickets):
-            st, _ = eng.poll(t, g.n, timeout_us=-1)
-            assert st == K.KCORE_OK
-        t_batch = time.perf_counter() - t0
-        sat = eng.stats()
-    rate_sat = G / t_batch
-    # served: Poisson arrivals at 0.7 x the saturated rate
-    lam = 0.7 * rate_sat
-    arrivals = graphgen.poisson_arrivals(G, lam, seed=1)
-    with K.BatchEngine(opts) as eng:
-        t0 = time.perf_counter()
-        tickets = []
-        for g, at in zip(graphs, arrivals):
-            delay = at - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(eng.submit_coo(g.n, g.src, g.dst))
-        for g, t in zip(graphs, tickets):
-            st, _ = eng.poll(t, g.n, timeout_us=-1)
-            assert st == K.KCORE_OK
-        t_served = time.perf_counter() - t0
-        served = eng.stats()
-    # the one-launch-per-graph server under the same arrivals (FIFO)
-    def fifo(arr):
-        end, out = 0.0, []
-        for at, sv in zip(arr, service):
-            start = max(at, end)
-            end = start + sv
-            out.append(end - at)
-        return np.array(out) * 1e3
-    lat = fifo(arrivals)
-    # both servers at 0.7 x what one launch per graph sustains
-    lam2 = 0.7 * G / t_one
-    arrivals2 = graphgen.poisson_arrivals(G, lam2, seed=2)
-    with K.BatchEngine(opts) as eng:
-        t0 = time.perf_counter()
-        tickets = []
-        for g, at in zip(graphs, arrivals2):
-            delay = at - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(eng.submit_coo(g.n, g.src, g.dst))
-        for g, t in zip(graphs, tickets):
-            st, _ = eng.poll(t, g.n, timeout_us=-1)
-            assert st == K.KCORE_OK
-        served2 = eng.stats()
-    lat2 = fifo(arrivals2)
-    line = {
-        "metric": "batched graphs/s", "value": rate_sat, "unit": "graphs/s", "n_gpus": 1,
-        "steps": 1, "warmup": 3, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "graph stream (n log-uniform 100..200000; ER/R-MAT/grid)",
-                   "graphs": G, "m_total": m_total, "arena_gib": args.arena_gib,
-                   "host_staging_gib": args.host_staging_gib,
-                   "chunk_sweeps": args.chunk_sweeps},
-        "one_launch_per_graph": {"graphs_per_s": G / t_one,
-                                 "p50_ms_at_served_rate": float(np.percentile(lat, 50)),
-                                 "p99_ms_at_served_rate": float(np.percentile(lat, 99)),
-                                 "mean_service_ms": 1e3 * float(np.mean(service))},
-        "batched": {"graphs_per_s": rate_sat, "launches": sat["launches"], "sweeps": sat["sweeps"],
-                    "edges_per_s": m_total / t_batch, "submit_s": t_submit,
-                    "busy_s": sat["busy_s"], "admit_s": sat["admit_s"], "sweep_s": sat["sweep_s"],
-                    "retire_s": sat["retire_s"], "admissions": sat["admissions"]},
-        "served": {"arrival_rate_per_s": lam, "graphs_per_s": G / t_served,
-                   "p50_ms": served["latency_p50_ms"], "p99_ms": served["latency_p99_ms"],
-                   "launches": served["launches"]},
-        "served_at_single_capacity": {
-            "arrival_rate_per_s": lam2,
-            "batched_p50_ms": served2["latency_p50_ms"], "batched_p99_ms": served2["latency_p99_ms"],
-            "one_launch_p50_ms": float(np.percentile(lat2, 50)),
-            "one_launch_p99_ms": float(np.percentile(lat2, 99))},
+    serve_one_launch(K, graphs[:3], None)            # warm-up
+    runs = {}
+    hashes = {}
+
+    def keep(name, res):
+        hashes[name] = [result_hash(r) for r in res]
+
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        wall, lat, res = serve_one_launch(K, graphs, None)
+        runs["one_launch_saturated"] = {"graphs_per_s": G / wall, "wall_s": wall}
+        keep("one_launch_saturated", res)
+        cap1 = G / wall
+        wall, lat, res, st, ov = serve_batched(K, opts, graphs, None)
+        runs["batched_saturated"] = {"graphs_per_s": G / wall, "wall_s": wall,
+                                     "launches": st["launches"], "admissions": st["admissions"],
+                                     "admitted_while_busy": st["admitted_while_busy"],
+                                     "busy_s": st["busy_s"], "admit_s": st["admit_s"],
+                                     "sweep_s": st["sweep_s"], "retire_s": st["retire_s"]}
+        keep("batched_saturated", res)
+        cap2 = G / wall
+        for tag, rate, seed in (("at_0.7x_one_launch", 0.7 * cap1, 1),
+                                ("at_0.7x_batched", 0.7 * cap2, 2)):
+            arr = graphgen.poisson_arrivals(G, rate, seed=seed)
+            wall, lat, res = serve_one_launch(K, graphs, arr)
+            p50, p99 = percentiles_ms(lat)
+            runs[f"one_launch_{tag}"] = {"arrival_rate_per_s": rate, "graphs_per_s": G / wall,
+                                         "p50_ms": p50, "p99_ms": p99}
+            keep(f"one_launch_{tag}", res)
+            wall, lat, res, st, ov = serve_batched(K, opts, graphs, arr)
+            p50, p99 = percentiles_ms(lat)
+            runs[f"batched_{tag}"] = {"arrival_rate_per_s": rate, "graphs_per_s": G / wall,
+                                      "p50_ms": p50, "p99_ms": p99, "launches": st["launches"],
+                                      "admitted_while_busy": st["admitted_while_busy"],
+                                      "admitted_into_busy_arena": ov}
+            keep(f"batched_{tag}", res)
+    del res, graphs
+    if after_timed is not None:
+        after_timed()
+    # every result against the oracle (outside the timed runs)
+    t0 = time.perf_counter()
+    workers = max(1, min(args.check_workers, os.cpu_count() or 1))
+    step = max(1, G // (workers * 8))
+    expect, m_total = [None] * G, 0
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        for part in ex.map(oracle_stream_hashes, range(0, G, step),
+                           [min(G, lo + step) for lo in range(0, G, step)]):
+            for i, h, m in part:
+                expect[i] = h
+                m_total += m
+    t_check = time.perf_counter() - t0
+    bad = {name: [i for i in range(G) if hs[i] != expect[i]] for name, hs in hashes.items()}
+    mismatches = {k: v[:10] for k, v in bad.items() if v}
+    if mismatches:
+        raise RuntimeError(f"stream results differ from the oracle: {mismatches}")
+    return {
+        "workload": "graph stream (first %d graphs; n log-uniform in [100, 200000]; "
+                    "ER avg degree 8 / R-MAT 8n samples / damaged grid)" % G,
+        "graphs": G, "m_total": m_total, "metric": "graphs/s and p50/p99 latency",
+        "arena_gib": args.arena_gib, "host_staging_gib": args.host_staging_gib,
+        "chunk_sweeps": args.chunk_sweeps,
+        "latency": "arrival (time.perf_counter before the request is handed in) to the result "
+                   "on the host; one launch per graph: coreness in the caller's buffer; batched: "
+                   "the engine's result-ready time on the same monotonic clock",
+        "runs": runs,
+        "batched_edges_per_s": m_total / runs["batched_saturated"]["wall_s"],
+        "results_checked": G * len(hashes), "graphs_checked": G, "check": "oracle coreness, "
+        "blake2b-128 of every result, all runs", "generate_s": t_gen, "check_s": t_check,
+        "clocks": clocks.summary(),
     }
-    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -565,7 +733,18 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stream":
-        run_stream(args)
+        import torch
+
+        import paper_2512_00233_gb300 as K
+        torch.cuda.set_device(0)
+        s = run_stream(args, K, torch)
+        r = s["runs"]["batched_saturated"]
+        line = {"metric": "batched graphs/s", "value": r["graphs_per_s"], "unit": "graphs/s",
+                "n_gpus": 1, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * r["wall_s"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic", "config": {"workload": s["workload"]},
+                "stream": s}
+        print(json.dumps(line), flush=True)
     else:
         run_ours(args)
 

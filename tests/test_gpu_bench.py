@@ -22,7 +22,9 @@ def run_bench(*args):
 
 
 def test_bench_line_has_the_contract_keys():
-    d = run_bench("--workload", "er10k", "--steps", "3", "--warmup", "3", "--cpu-budget-s", "1")
+    d = run_bench("--workload", "er10k", "--steps", "3", "--warmup", "3", "--cpu-budget-s", "1",
+                  "--stream-count", "40", "--check-workers", "2", "--arena-gib", "1",
+                  "--host-staging-gib", "1")
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
               "gpu_launches", "roofline", "cpu_baseline", "clocks"):
@@ -36,6 +38,14 @@ def test_bench_line_has_the_contract_keys():
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    s = d["stream"]
+    assert s["graphs"] == 40 and s["results_checked"] == 40 * len(s["runs"])
+    for run in ("one_launch_saturated", "batched_saturated"):
+        assert s["runs"][run]["graphs_per_s"] > 0
+    for tag in ("at_0.7x_one_launch", "at_0.7x_batched"):
+        for server in ("one_launch", "batched"):
+            r = s["runs"][f"{server}_{tag}"]
+            assert r["p99_ms"] >= r["p50_ms"] > 0
 
 
 def test_reference_arm_line():
