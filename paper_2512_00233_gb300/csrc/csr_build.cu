@@ -1147,7 +1147,7 @@ kcore_status cuda_fail(cudaError_t e, const char* what, std::string* err) {
 
 int grid_for(long long items, int per_block) {
     return (int)std::max<long long>(1, std::min<long long>((items + per_block - 1) / per_block,
-                                                           152LL * 64));
+                                                           (long long)sm_count() * 64));
 }
 
 template <typename Off>
@@ -1244,7 +1244,7 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
         const size_t smem = sizeof(uint32_t) * 2 * kBigMax;  // two merge buffers
         KC_TRY(cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem), "smem attribute");
-        k_sort_big<<<(unsigned)std::min<unsigned>(hbc.n_big, 152u * 2u), kBigT, smem, st>>>(
+        k_sort_big<<<(unsigned)std::min<unsigned>(hbc.n_big, (unsigned)sm_count() * 2u), kBigT, smem, st>>>(
             big, bc, off, seg, ucnt);
         count_launch();
         KC_TRY(cudaGetLastError(), "sort big rows");
@@ -1256,7 +1256,7 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
         KC_TRY(tmp.get(&alt, (size_t)H), "hub keys");
         KC_TRY(tmp.get(&hoff, (size_t)hbc.n_huge + 1), "hub offsets");
         KC_TRY(exclusive_scan(HubLen{huge, off}, (long long)hbc.n_huge, hoff, true, st, &tmp), "hub offsets");
-        const unsigned g = std::min<unsigned>(hbc.n_huge, 152u * 4u);
+        const unsigned g = std::min<unsigned>(hbc.n_huge, (unsigned)sm_count() * 4u);
         k_huge_keys<<<g, 512, 0, st>>>(huge, hbc.n_huge, hoff, off, seg, keys);
         count_launch();
         KC_TRY(cudaGetLastError(), "hub keys");
@@ -1379,7 +1379,7 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
         k_count_coo<<<grid_for(samples / kSortProbe + 256, 256), 256, 0, st>>>(src, dst, samples, (int)n,
                                                                              cnt, bc, kSortProbe);
         count_launch();
-        k_heavy<<<(unsigned)std::min<long long>(grid_for(n, 256), 152LL * 4), 256, 0, st>>>(
+        k_heavy<<<(unsigned)std::min<long long>(grid_for(n, 256), (long long)sm_count() * 4), 256, 0, st>>>(
             cnt, n, kSmallMax / kSortProbe, bc);
         count_launch();
         KC_TRY(cudaGetLastError(), "row classes");
