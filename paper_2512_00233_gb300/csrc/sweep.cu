@@ -576,13 +576,21 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* 
 }
 
 // Warp tier, degrees above 32 * kMedR (up to kMedBig): one warp per vertex.
-// The first pass gathers the estimates kMedU per lane at a time, keeps
-// y = min(x, k) as 16 bits in the warp's slice of shared memory and counts
-// x >= k; once that count reaches k the estimate stands and the pass stops.
-// Otherwise h < k is found by bisection on t with counts of y >= t taken from
-// shared memory, and a last pass pushes the neighbours with y > h.
+// The first pass gathers the estimates kMedU per lane at a time and keeps, as
+// 16 bits in the warp's slice of shared memory, y = min(x, k + 1) (12 bits)
+// and the neighbour's degree tier (bits 14-15), counting x >= k; once that
+// count reaches k the estimate stands and the pass stops.  Otherwise h < k is
+// found by bisection on t with counts of y >= t over the staged words (eight
+// per 16-byte read; the slice is zero-padded to a whole number of reads), and
+// a last pass pushes the neighbours with y > h.  A neighbour staged with
+// y <= k is pushed on its staged value: the estimates only decrease, so the
+// value read now would be at most y, the refined condition x <= k holds, and
+// a value that dropped to h or below since only over-activates.  Only a
+// neighbour staged above k is gathered again for the refined test.
 constexpr int kMedU = 4;
 constexpr int kMedSlice = kMedBig / 2;  // words per warp
+constexpr uint32_t kStageVal = 0x0fffu;   // value bits of a staged word
+constexpr int kStageTier = 14;            // tier bits of a staged word
 
 template <typename Off>
 __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
@@ -607,20 +615,23 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
     int ck = 0, read = d;
     bool stands = false;
     for (int j0 = 0; j0 < d; j0 += 32 * kMedU) {
-        int vs[kMedU], xs[kMedU];
+        int vs[kMedU];
+        uint32_t xw[kMedU];
 #pragma unroll
         for (int r = 0; r < kMedU; r++) {
             const int j = j0 + r * 32 + lane;
             vs[r] = j < d ? __ldg(colb + j) : -1;
         }
 #pragma unroll
-        for (int r = 0; r < kMedU; r++) xs[r] = vs[r] >= 0 ? (int)(est_load(a.est + vs[r]) & kEstMask) : -1;
+        for (int r = 0; r < kMedU; r++) xw[r] = vs[r] >= 0 ? est_load(a.est + vs[r]) : 0u;
         int c = 0;
 #pragma unroll
         for (int r = 0; r < kMedU; r++) {
-            if (xs[r] >= 0) {
-                c += xs[r] >= k ? 1 : 0;
-                sx[j0 + r * 32 + lane] = (uint16_t)(xs[r] < k ? xs[r] : k);
+            if (vs[r] >= 0) {
+                const int x = (int)(xw[r] & kEstMask);
+                c += x >= k ? 1 : 0;
+                const uint32_t y = (uint32_t)(x <= k ? x : k + 1);
+                sx[j0 + r * 32 + lane] = (uint16_t)(y | ((xw[r] >> kEstBits) << kStageTier));
             }
         }
         ck += (int)__reduce_add_sync(kFull, (unsigned)c);
@@ -636,13 +647,23 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
         __syncwarp();
         return;
     }
+    const int padded = (d + 255) & ~255;  // whole 16-byte reads for every lane
+    for (int j = d + lane; j < padded; j += 32) sx[j] = 0;
     __syncwarp();
-    int lo = 0, hi = k - 1;  // count(y >= 0) = d >= 0 holds; h < k
+    const uint4* sv = (const uint4*)slice;
+    const int nv = padded >> 8;  // 16-byte reads per lane
+    int lo = 0, hi = k - 1;      // count(y >= 0) = d >= 0 holds; h < k
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
+        const uint32_t mid2 = (uint32_t)mid * 0x00010001u;
+        const uint32_t vm = kStageVal * 0x00010001u;
         int c = 0;
-        for (int j = lane; j < d; j += 32) c += sx[j] >= mid ? 1 : 0;
-        c = (int)__reduce_add_sync(kFull, (unsigned)c);
+        for (int i = 0; i < nv; i++) {
+            const uint4 q = sv[i * 32 + lane];
+            c += __popc(__vcmpgeu2(q.x & vm, mid2)) + __popc(__vcmpgeu2(q.y & vm, mid2)) +
+                 __popc(__vcmpgeu2(q.z & vm, mid2)) + __popc(__vcmpgeu2(q.w & vm, mid2));
+        }
+        c = (int)__reduce_add_sync(kFull, (unsigned)c) >> 4;  // 16 bits set per match
         if (c >= mid) lo = mid;
         else hi = mid - 1;
     }
@@ -660,17 +681,27 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const O
     for (int j0 = 0; j0 < d; j0 += 32 * kMedU) {
         int vs[kMedU];
         uint32_t xw[kMedU];
-        uint32_t cand = 0;
+        uint32_t cand = 0, again = 0;
 #pragma unroll
         for (int r = 0; r < kMedU; r++) {
             const int j = j0 + r * 32 + lane;
-            const bool want = j < d && (int)sx[j] > h;
+            const uint32_t y = j < d ? (uint32_t)sx[j] : 0u;
+            const int yv = (int)(y & kStageVal);
+            const bool want = j < d && yv > h;
             vs[r] = want ? __ldg(colb + j) : -1;
+            xw[r] = ((y >> kStageTier) << kEstBits) | (uint32_t)yv;
+            if (want) {
+                if (yv <= k) cand |= 1u << r;
+                else again |= 1u << r;
+            }
         }
+        if (again) {
 #pragma unroll
-        for (int r = 0; r < kMedU; r++) {
-            xw[r] = vs[r] >= 0 ? est_load(a.est + vs[r]) : 0u;
-            if (vs[r] >= 0 && (int)(xw[r] & kEstMask) > h) cand |= 1u << r;
+            for (int r = 0; r < kMedU; r++)
+                if ((again >> r) & 1u) xw[r] = est_load(a.est + vs[r]);
+#pragma unroll
+            for (int r = 0; r < kMedU; r++)
+                if (((again >> r) & 1u) && (int)(xw[r] & kEstMask) > h) cand |= 1u << r;
         }
         warp_push_n<kMedU>(S, Q, cand, h, k, vs, xw, acc);
     }
