@@ -17,6 +17,8 @@ is the coreness):
   vertex marks itself done once evaluated, and for a done vertex (or one not
   in the frontier) the refined test is applied to a value of est[v] read
   after seeing the mark (v's final value of the sweep);
+* marks made later than the evaluation (the kernel's warp tier marks the
+  vertices of one work grab together, after the grab) keep that rule safe;
 * applying the refined test to the value read before the mark is unsafe;
 * warm starts (dynamic maintenance): after deleting edges, starting from the
   old coreness with only the deleted edges' endpoints active, and after
@@ -54,6 +56,7 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000, start=None, active=None):
         rng.shuffle(order)
         nxt = set()
         done = set()
+        pending = []                          # deferred marks (refined_done_deferred)
 
         def read(v):                          # stale or fresh, at random
             return start[v] if rng.random() < 0.5 else est[v]
@@ -61,7 +64,10 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000, start=None, active=None):
         for u in order:
             k = est[u]
             h = capped_hindex([read(v) for v in adj[u]], k)
-            done.add(u)
+            if rule == "refined_done_deferred":
+                pending.append(u)             # marked with a later group, after its store
+            else:
+                done.add(u)
             if h >= k:
                 continue
             est[u] = h
@@ -71,7 +77,7 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000, start=None, active=None):
                     push = h < x
                 elif rule == "refined_frontier":
                     push = h < x and (x <= k or v in frontier)
-                elif rule == "refined_done":
+                elif rule in ("refined_done", "refined_done_deferred"):
                     if h < x and x > k and v in frontier and v not in done:
                         push = True           # v may still be reading u's old value
                     elif h < x and x > k:
@@ -85,6 +91,9 @@ def run_async(n, adj, rule, rng, max_sweeps=10_000, start=None, active=None):
                     push = h < x and x <= k
                 if push:
                     nxt.add(v)
+            if pending and (len(pending) >= 4 or rng.random() < 0.3):
+                done.update(pending)
+                pending = []
         frontier = nxt
     return est
 
@@ -112,7 +121,7 @@ def test_safe_rules_always_reach_the_coreness():
         n = rng.randint(2, 24)
         adj = random_graph(rng, n, rng.uniform(0.1, 0.6))
         core = coreness(n, adj)
-        for rule in ("simple", "refined_frontier", "refined_done"):
+        for rule in ("simple", "refined_frontier", "refined_done", "refined_done_deferred"):
             for _ in range(3):
                 assert run_async(n, adj, rule, rng) == core, (trial, rule)
 
