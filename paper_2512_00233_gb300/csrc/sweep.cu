@@ -517,14 +517,11 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
 // One warp per vertex, up to 32*R neighbour estimates held in registers; the
 // count of neighbours >= t comes from a warp reduction, and h by bisection on
 // t after the no-change test t = k.
-template <typename Off, int R>
-__device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
-                                           int u, Acc& acc) {
+template <int R>
+__device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, int u, long long b, int d,
+                                           uint32_t w, Acc& acc) {
     const SweepArgs& a = *S.a;
     const int lane = threadIdx.x & 31;
-    const long long b = (long long)rp[u];
-    const int d = (int)((long long)rp[u + 1] - b);
-    const uint32_t w = est_load(a.est + u);
     const int k = (int)(w & kEstMask);
     if (lane == 0) {
         acc.evaluated += 1;
@@ -592,15 +589,11 @@ constexpr int kMedSlice = kMedBig / 2;  // words per warp
 constexpr uint32_t kStageVal = 0x0fffu;   // value bits of a staged word
 constexpr int kStageTier = 14;            // tier bits of a staged word
 
-template <typename Off>
-__device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, const Off* __restrict__ rp,
-                                               int u, uint32_t* slice, Acc& acc) {
+__device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, int u, long long b, int d,
+                                               uint32_t w, uint32_t* slice, Acc& acc) {
     const SweepArgs& a = *S.a;
     const int lane = threadIdx.x & 31;
     uint16_t* sx = (uint16_t*)slice;
-    const long long b = (long long)rp[u];
-    const int d = (int)((long long)rp[u + 1] - b);
-    const uint32_t w = est_load(a.est + u);
     const int k = (int)(w & kEstMask);
     if (lane == 0) {
         acc.evaluated += 1;
@@ -1287,12 +1280,30 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
         // when the tier is small, so that every warp gets some)
         if (c1 > 0) {
             const unsigned wi = max(1u, min((unsigned)a.med_chunk, c1 / warps_all));
+            // the grab's vertex ids, row bounds and estimates are loaded together,
+            // one vertex per lane, before the first evaluation (only u writes
+            // est[u], so the early read is its value when u is evaluated)
             run_tier(&ctl->cursor[cur][1], c1, wi, [&](unsigned i0, unsigned i1) {
-                for (unsigned i = i0; i < i1; i++) {
-                    const int u = list_load(S.lcur + a.tier_off[1] + i);
-                    const long long du = (long long)rp[u + 1] - (long long)rp[u];
-                    if (du <= 32 * kMedR) med_vertex<Off, kMedR>(S, Q, rp, u, acc);
-                    else med_big_vertex<Off>(S, Q, rp, u, s_pool + wid * kMedSlice, acc);
+                for (unsigned base = i0; base < i1; base += 32u) {
+                    const unsigned j = base + (unsigned)lane;
+                    int u = 0;
+                    long long rb = 0, re = 0;
+                    uint32_t w = 0;
+                    if (j < i1) {
+                        u = list_load(S.lcur + a.tier_off[1] + j);
+                        rb = (long long)rp[u];
+                        re = (long long)rp[u + 1];
+                        w = est_load(a.est + u);
+                    }
+                    const unsigned cnt = min(32u, i1 - base);
+                    for (unsigned t = 0; t < cnt; t++) {
+                        const int ut = __shfl_sync(kFull, u, (int)t);
+                        const long long bt = __shfl_sync(kFull, rb, (int)t);
+                        const int dt = (int)(__shfl_sync(kFull, re, (int)t) - bt);
+                        const uint32_t wt = __shfl_sync(kFull, w, (int)t);
+                        if (dt <= 32 * kMedR) med_vertex<kMedR>(S, Q, ut, bt, dt, wt, acc);
+                        else med_big_vertex(S, Q, ut, bt, dt, wt, s_pool + wid * kMedSlice, acc);
+                    }
                 }
             });
         }
