@@ -382,12 +382,20 @@ def run_ours(args):
     tuned = None
     t_tune = 0.0
     if args.autotune:
+        # the vertex numbering first (fixed when a graph is made), then the
+        # sweep knobs on a graph with that numbering
         from paper_2512_00233_gb300 import autotune
         t0 = time.perf_counter()
-        with K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes) as gt:
+        order, order_ms = autotune.pick_order(
+            lambda r: K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes, options=K.default_options(relabel=r)),
+            reps=2)
+        with K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes, options=K.default_options(relabel=order)) as gt:
             opts, _ = autotune.autotune(gt, reps=2, passes=1, cache=None)
+        opts.relabel = order
         t_tune = time.perf_counter() - t0
         tuned = {k: getattr(opts, k) for k in autotune.SPACE}
+        tuned["relabel"] = order
+        tuned["relabel_sweep_ms"] = {str(k): v for k, v in order_ms.items()}
 
     def step_device():
         g = K.Graph.from_coo(g0.n, src_d, dst_d, rp_bytes, options=opts)

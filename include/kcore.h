@@ -109,6 +109,22 @@ typedef struct kcore_options {
                                than 32 entries hold half of the entries or more
                                (estimated from every 16th run of 256 samples).
                                The cleaned graph is the same either way.          */
+    int32_t  relabel;       /* vertex numbering of a graph built from edge samples
+                               (kcore_create_coo): 1 = renumbered by descending
+                               degree, 2 = by ascending degree, -1 = the input's
+                               numbering, 0 (default) = descending degree when
+                               the sample-based cleaner is chosen automatically
+                               for hub-dominated inputs (see build_sort), else
+                               the input's.  Renumbering packs the estimates of
+                               high-degree vertices into few cache lines and
+                               lists them together in every row; the cleaner
+                               renumbers while it sorts (it takes the sorted
+                               build).  Internal: coreness, warm starts and
+                               kcore_copy_csr use the caller's ids (the copy of
+                               a renumbered graph is rebuilt on the device, at
+                               about the cost of a create).  Fixed at creation:
+                               kcore_set_options does not change it.  Ignored by
+                               kcore_create and by batches.                      */
 } kcore_options;
 
 /* Fill `opt` with the defaults. */

@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
     _fields_ = [("struct_size", c_u32), ("t_lo", c_i32), ("t_hi", c_i32), ("block", c_i32),
                 ("low_chunk", c_i32), ("med_chunk", c_i32), ("tail_max", c_i32),
                 ("ctas_per_sm", c_i32), ("max_ctas", c_i32), ("max_sweeps", c_i64),
-                ("timeout_s", ctypes.c_double), ("build_sort", c_i32)]
+                ("timeout_s", ctypes.c_double), ("build_sort", c_i32), ("relabel", c_i32)]
 
 
 class RunStats(ctypes.Structure):

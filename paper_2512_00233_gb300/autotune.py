@@ -1,9 +1,10 @@
 """Autotuner of the sweep engine's launch knobs.
 
-Coordinate descent over the degree-tier thresholds (t_lo, t_hi), the CTA size,
-the work-grab sizes and the single-CTA tail threshold: each knob in turn is
-set to each of its candidate values with the others fixed, the graph is
-decomposed a few times, and the value with the lowest median sweep-kernel time
+Coordinate descent over the degree-tier thresholds (t_lo, t_hi), the CTA
+size, the work-grab sizes and the single-CTA tail threshold: each knob in
+turn is set to each of its candidate values with the others fixed, the graph
+is decomposed a few times, and the value with the lowest median sweep-kernel
+time
 (CUDA events recorded by the library around the launch) is kept.  Two passes.
 Every candidate run is checked to give the same coreness as the first.
 
@@ -93,6 +94,27 @@ def autotune(graph: Graph, reps: int = 3, passes: int = 2, space: dict | None = 
             json.dump(data, f, indent=1, sort_keys=True)
         os.replace(tmp, cache)
     return opts, trials
+
+
+def pick_order(make_graph, reps: int = 3, orders=(1, 2, -1)):
+    """The vertex numbering (kcore_options.relabel, fixed when a graph is made)
+    with the lowest median sweep time: make_graph(relabel) builds the graph.
+    Every candidate is checked to give the same coreness.  Returns (relabel,
+    {relabel: ms})."""
+    times, ref = {}, None
+    for r in orders:
+        with make_graph(r) as g:
+            out = g.run()
+            if ref is None:
+                ref = out.cpu()
+            assert bool((out.cpu() == ref).all()), "numbering changed the result"
+            ms = []
+            for _ in range(reps):
+                g.run(out=out)
+                ms.append(g.stats()["ms_sweep"])
+            times[r] = statistics.median(ms)
+    best = min(times, key=times.get)
+    return best, times
 
 
 def tuned_options(graph: Graph, cache: str = DEFAULT_CACHE) -> Options | None:

@@ -47,6 +47,7 @@ kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
     if (in->max_sweeps) out->max_sweeps = in->max_sweeps;
     if (in->timeout_s > 0) out->timeout_s = in->timeout_s;
     if (in->build_sort) out->build_sort = in->build_sort;
+    if (in->relabel) out->relabel = in->relabel;
     if (out->t_lo < 1 || out->t_lo > 32) return fail(KCORE_ERR_INVALID, "t_lo must be in 1..32");
     if (out->t_hi < out->t_lo || out->t_hi > kMedBig)
         return fail(KCORE_ERR_INVALID, "t_hi must be in t_lo..2048");
@@ -59,6 +60,8 @@ kcore_status normalize_options(const kcore_options* in, kcore_options* out) {
         return fail(KCORE_ERR_INVALID, "negative option");
     if (out->build_sort < -1 || out->build_sort > 1)
         return fail(KCORE_ERR_INVALID, "build_sort must be -1, 0 or 1");
+    if (out->relabel < -1 || out->relabel > 2)
+        return fail(KCORE_ERR_INVALID, "relabel must be -1, 0, 1 or 2");
     return KCORE_OK;
 }
 
@@ -68,7 +71,11 @@ using namespace kc;
 
 struct kcore_graph {
     int device = 0;
-    DevCsr csr;
+    DevCsr csr;                // the cleaned CSR the sweeps read (renumbered when relabeled)
+    bool relabeled = false;    // csr uses new ids: new_of_old[caller's id]
+    int* new_of_old = nullptr; // the numbering (n each), when relabeled
+    int* old_of_new = nullptr;
+    int* hout = nullptr;       // coreness in the caller's ids before a copy to host memory
     kcore_options opt{};
     uint32_t* est0 = nullptr;
     uint32_t* est = nullptr;
@@ -113,6 +120,9 @@ void release(kcore_graph* g) {
     cudaDeviceSynchronize();
     dfree(g->csr.row_ptr);
     dfree(g->csr.col);
+    dfree(g->new_of_old);
+    dfree(g->old_of_new);
+    dfree(g->hout);
     dfree(g->state);  // est0, est, lists, bitmaps, ctl, trace, dtier
     dfree(g->upd_list);
     dfree(g->upd_val);
@@ -319,9 +329,14 @@ kcore_status kcore_create_coo(int64_t n, int64_t nnz, const int32_t* src, const 
     }
     std::string err;
     if (s == KCORE_OK) {
-        s = clean_from_coo(n, nnz, ds, dd, row_ptr_bytes, g->opt.build_sort, st, &g->csr,
-                           &err);
+        s = clean_from_coo(n, nnz, ds, dd, row_ptr_bytes, g->opt.build_sort, g->opt.relabel, st,
+                           &g->csr, &g->new_of_old, &g->old_of_new, &err);
         if (s != KCORE_OK) set_error(err);
+        g->relabeled = g->new_of_old != nullptr;
+        if (s == KCORE_OK && g->relabeled) {
+            s = dmalloc((void**)&g->hout, sizeof(int) * std::max<int64_t>(n, 1), &err, st);
+            if (s != KCORE_OK) set_error(err);
+        }
     }
     if (tmp_s) cudaFreeAsync(tmp_s, st);
     if (tmp_d) cudaFreeAsync(tmp_d, st);
@@ -433,9 +448,9 @@ kcore_status kcore_set_options(kcore_graph* g, const kcore_options* opt, void* c
     const bool rebin = o.t_lo != g->opt.t_lo || o.t_hi != g->opt.t_hi;
     g->opt = o;
     g->opt_epoch++;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!rebin) return KCORE_OK;
     std::string err;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     s = tier_split(g->csr.n, g->csr.row_ptr, g->csr.off_bytes, o.t_lo, o.t_hi, g->est0,
                    g->init_list, g->dtier, st, &err);
     if (s != KCORE_OK) return fail(s, err);
@@ -517,7 +532,9 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
             e = launch_warm_init(a, g->csr.row_ptr, g->est0, warm.start, warm.frontier, warm.nf, st);
         if (e != cudaSuccess) return cuda_status(e, "warm start");
     }
-    a.out = (flags & KCORE_OUT_DEVICE) ? coreness_out : (int*)g->est;
+    a.perm = g->relabeled ? g->new_of_old : nullptr;
+    int* host_src = g->relabeled ? g->hout : (int*)g->est;  // coreness before the copy to the host
+    a.out = (flags & KCORE_OUT_DEVICE) ? coreness_out : host_src;
 
     // Grid: enough CTAs for the first sweep's work, at most the co-resident maximum.
     const long long work = n + g->csr.nnz;
@@ -531,7 +548,7 @@ kcore_status enqueue_run(kcore_graph* g, int32_t* coreness_out, uint32_t flags, 
     if (e == cudaSuccess) e = record(g->ev[EV_S1], st, capture);
     if (e != cudaSuccess) return cuda_status(e, "sweep launch");
     if (!(flags & KCORE_OUT_DEVICE) && n)
-        e = cudaMemcpyAsync(coreness_out, g->est, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(coreness_out, host_src, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->hctl, g->ctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = record(g->ev[EV_R1], st, capture);
@@ -632,9 +649,23 @@ kcore_status kcore_run_from(kcore_graph* g, const int32_t* start, const int32_t*
         w.frontier = frontier ? tmp_front : nullptr;
     }
     w.nf = frontier ? nfrontier : 0;
+    int *map_start = nullptr, *map_front = nullptr;
+    if (s == KCORE_OK && g->relabeled && n > 0) {  // the caller's ids -> the renumbered ones
+        cudaError_t e = pool_alloc((void**)&map_start, sizeof(int) * n, st);
+        if (e == cudaSuccess && w.frontier)
+            e = pool_alloc((void**)&map_front, sizeof(int) * std::max<long long>(w.nf, 1), st);
+        if (e == cudaSuccess)
+            e = launch_relabel_start(w.start, w.frontier, w.nf, n, g->old_of_new, g->new_of_old,
+                                     map_start, map_front, st);
+        if (e != cudaSuccess) s = cuda_status(e, "warm start renumbering");
+        w.start = map_start;
+        if (w.frontier) w.frontier = map_front;
+    }
     if (s == KCORE_OK && n > 0) s = enqueue_run(g, coreness_out, flags, st, false, w);
     if (tmp_start) cudaFreeAsync(tmp_start, st);
     if (tmp_front) cudaFreeAsync(tmp_front, st);
+    if (map_start) cudaFreeAsync(map_start, st);
+    if (map_front) cudaFreeAsync(map_front, st);
     if (s != KCORE_OK) return s;
     if (n == 0) return KCORE_OK;
     g->pending = true;
@@ -662,11 +693,43 @@ kcore_status kcore_copy_csr(const kcore_graph* g, void* row_ptr_out, int32_t* co
     if (!g) return fail(KCORE_ERR_INVALID, "graph is NULL");
     const cudaMemcpyKind kind =
         (flags & KCORE_OUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    DevCsr c = g->csr;
+    if (g->relabeled) {
+        // the caller's ids: the renumbered entries mapped back and cleaned
+        // again (sorted build, no renumbering); rare, so not kept
+        std::string err;
+        int *src = nullptr, *dst = nullptr;
+        cudaError_t ce = pool_alloc((void**)&src, sizeof(int) * std::max<int64_t>(g->csr.nnz, 1), 0);
+        if (ce == cudaSuccess) ce = pool_alloc((void**)&dst, sizeof(int) * std::max<int64_t>(g->csr.nnz, 1), 0);
+        if (ce == cudaSuccess)
+            ce = launch_relabel_unmap(g->csr.row_ptr, g->csr.off_bytes, g->csr.col, g->csr.n, g->csr.nnz,
+                                      g->old_of_new, src, dst, 0);
+        kcore_status s = ce == cudaSuccess ? KCORE_OK : cuda_status(ce, "kcore_copy_csr");
+        c = DevCsr();
+        if (s == KCORE_OK) {
+            s = clean_from_coo(g->csr.n, g->csr.nnz, src, dst, g->csr.off_bytes, 1, -1, 0, &c, nullptr,
+                               nullptr, &err);
+            if (s != KCORE_OK) set_error(err);
+        }
+        if (src) cudaFreeAsync(src, 0);
+        if (dst) cudaFreeAsync(dst, 0);
+        if (s == KCORE_OK && cudaStreamSynchronize(0) != cudaSuccess) s = cuda_status(cudaGetLastError(), "sync");
+        if (s != KCORE_OK) {
+            dfree(c.row_ptr, 0);
+            dfree(c.col, 0);
+            return s;
+        }
+        c.nnz = g->csr.nnz;
+    }
     cudaError_t e = cudaSuccess;
-    if (row_ptr_out)
-        e = cudaMemcpy(row_ptr_out, g->csr.row_ptr, (size_t)g->csr.off_bytes * (g->csr.n + 1), kind);
-    if (e == cudaSuccess && col_idx_out && g->csr.nnz)
-        e = cudaMemcpy(col_idx_out, g->csr.col, sizeof(int) * g->csr.nnz, kind);
+    if (row_ptr_out) e = cudaMemcpy(row_ptr_out, c.row_ptr, (size_t)c.off_bytes * (c.n + 1), kind);
+    if (e == cudaSuccess && col_idx_out && c.nnz)
+        e = cudaMemcpy(col_idx_out, c.col, sizeof(int) * c.nnz, kind);
+    if (g->relabeled) {
+        dfree(c.row_ptr, 0);
+        dfree(c.col, 0);
+        cudaStreamSynchronize(0);
+    }
     if (e != cudaSuccess) return cuda_status(e, "kcore_copy_csr");
     return KCORE_OK;
 }

@@ -1003,14 +1003,14 @@ __device__ __forceinline__ int tier_of(long long d, int t_lo, int t_hi) {
 
 template <typename Off>
 __global__ void __launch_bounds__(kTsT) k_tier_count(const Off* __restrict__ rp, int n, int t_lo,
-                                                     int t_hi, uint32_t* cnt, int nb, int* bad) {
+                                                     int t_hi, uint32_t* cnt, int nb, TierOut* out) {
     __shared__ uint32_t c[kTiers];
     if (threadIdx.x < kTiers) c[threadIdx.x] = 0;
     __syncthreads();
     const long long v = (long long)blockIdx.x * kTsT + threadIdx.x;
     if (v < n) {
         const long long d = (long long)(rp[v + 1] - rp[v]);
-        if (d > (long long)kEstMask) *bad = 1;
+        if (d > (long long)kEstMask) out->bad = 1;
         atomicAdd(&c[tier_of(d, t_lo, t_hi)], 1u);
     }
     __syncthreads();
@@ -1059,14 +1059,19 @@ __global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int
 // written.  No per-row atomics on hot rows and no per-row sorts.  (Making the
 // keys inside the first radix pass instead was slower.)
 __global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst, long long S,
-                          int n, ulonglong2* __restrict__ keys, BuildCtl* bc) {
+                          int n, ulonglong2* __restrict__ keys, BuildCtl* bc,
+                          const int* __restrict__ remap) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
          i += (long long)gridDim.x * blockDim.x) {
-        const int s = src[i], d = dst[i];
+        int s = src[i], d = dst[i];
         ulonglong2 k = make_ulonglong2(kNoKey, kNoKey);
         if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n) {
             bc->bad = 1;
         } else if (s != d) {
+            if (remap) {
+                s = __ldg(remap + s);
+                d = __ldg(remap + d);
+            }
             k.x = ((unsigned long long)(unsigned)s << 32) | (unsigned)d;
             k.y = ((unsigned long long)(unsigned)d << 32) | (unsigned)s;
         }
@@ -1297,7 +1302,7 @@ kcore_status finish(Temp& tmp, int64_t n, long long N, uint32_t* cnt, BuildCtl* 
 // range flag.
 kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, const int* dst,
                           BuildCtl* bc, int off_bytes, cudaStream_t st, DevCsr* out,
-                          std::string* err) {
+                          std::string* err, const int* remap) {
     const long long N = 2 * S, nn = std::max<int64_t>(n, 1);
     const long long nt = (N + kRsTile - 1) / kRsTile;
     unsigned long long *keys = nullptr, *alt = nullptr, *sorted = nullptr;
@@ -1312,7 +1317,7 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     KC_TRY(tmp.get(&tsum, (size_t)nt), "tile counts");
     KC_TRY(tmp.get(&toff, (size_t)nt + 1), "tile offsets");
     KC_TRY(cudaMemsetAsync(ucnt, 0, sizeof(uint32_t) * nn, st), "memset");
-    k_sb_keys<<<grid_for(S, 256), 256, 0, st>>>(src, dst, S, (int)n, (ulonglong2*)keys, bc);
+    k_sb_keys<<<grid_for(S, 256), 256, 0, st>>>(src, dst, S, (int)n, (ulonglong2*)keys, bc, remap);
     count_launch();
     KC_TRY(cudaGetLastError(), "keys");
     const int bits = id_bits(n);
@@ -1352,13 +1357,122 @@ cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long lo
     return exclusive_scan(ReadU32{in}, N, out, true, st);
 }
 
+namespace {
+
+// ------------------------------------------------------------------ relabeling by degree
+// Renumbering the vertices in order of degree packs the estimates of the
+// high-degree vertices (the ones most adjacency entries point to) into few
+// cache lines, and the cleaned rows, sorted by the new ids, then list the
+// high-degree neighbours together: a warp's gathers of their estimates touch
+// few sectors, and the no-change test of a hub meets its supporters early.
+// The sorted build renumbers before it sorts, so the cleaned CSR comes out in
+// the new ids with sorted rows at no extra sorting cost.  The order is that
+// of the probe counts (every kSortProbe-th run of samples, an estimate of the
+// degree), descending or ascending, ties by old id (a stable sort).
+__global__ void k_rl_keys(const uint32_t* __restrict__ cnt, long long n, int descending,
+                          unsigned long long* __restrict__ keys) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long c = cnt[v];
+        const unsigned long long ck = descending ? 0xffffffffull - c : c;
+        keys[v] = (ck << 32) | (unsigned long long)v;
+    }
+}
+
+__global__ void k_rl_perm(const unsigned long long* __restrict__ sorted, long long n,
+                          int* __restrict__ old_of_new, int* __restrict__ new_of_old) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int old = (int)(uint32_t)(sorted[i] & 0xffffffffull);
+        old_of_new[i] = old;
+        new_of_old[old] = (int)i;
+    }
+}
+
+// The entries of a renumbered CSR as samples in the caller's ids (both
+// directions are present already): row of entry p by bisection of row_ptr.
+template <typename Off>
+__global__ void k_rl_unmap(const Off* __restrict__ rp, const int* __restrict__ col, long long n,
+                           long long nnz, const int* __restrict__ old_of_new, int* __restrict__ src,
+                           int* __restrict__ dst) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz;
+         p += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = n - 1;  // last row whose start is <= p
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if ((long long)rp[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        src[p] = old_of_new[lo];
+        dst[p] = old_of_new[col[p]];
+    }
+}
+
+__global__ void k_rl_start(const int* __restrict__ start, const int* __restrict__ frontier, long long nf,
+                           long long n, const int* __restrict__ old_of_new,
+                           const int* __restrict__ new_of_old, int* __restrict__ start2,
+                           int* __restrict__ frontier2) {
+    const long long total = n > nf ? n : nf;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < n) start2[i] = start[old_of_new[i]];
+        if (frontier && i < nf) {
+            const int f = frontier[i];
+            frontier2[i] = (f >= 0 && f < n) ? new_of_old[f] : f;
+        }
+    }
+}
+
+// The renumbering of a build: new_of_old / old_of_new (n each, allocated
+// here) from the probe counts in cnt.
+kcore_status make_renumbering(Temp& tmp, int64_t n, const uint32_t* cnt, int descending, cudaStream_t st,
+                              int** new_of_old, int** old_of_new, std::string* err) {
+    const long long nn = std::max<int64_t>(n, 1);
+    const long long nt = (nn + kRsTile - 1) / kRsTile;
+    unsigned long long *keys = nullptr, *alt = nullptr, *sorted = nullptr;
+    KC_TRY(tmp.get(&keys, (size_t)nn), "renumbering keys");
+    KC_TRY(tmp.get(&alt, (size_t)nn), "renumbering keys");
+    (void)nt;
+    kcore_status s = dmalloc((void**)new_of_old, sizeof(int) * nn, err, st);
+    if (s == KCORE_OK) s = dmalloc((void**)old_of_new, sizeof(int) * nn, err, st);
+    if (s != KCORE_OK) return s;
+    const int g = grid_for(n, 256);
+    k_rl_keys<<<g, 256, 0, st>>>(cnt, n, descending, keys);
+    count_launch();
+    KC_TRY(cudaGetLastError(), "renumbering keys");
+    KC_TRY(radix_sort(KeyIn{keys}, n, alt, keys, 0, 32, st, &sorted, &tmp, (int*)nullptr), "renumbering sort");
+    k_rl_perm<<<g, 256, 0, st>>>(sorted, n, *old_of_new, *new_of_old);
+    count_launch();
+    KC_TRY(cudaGetLastError(), "renumbering");
+    return KCORE_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_relabel_unmap(const void* row_ptr, int off_bytes, const int* col, long long n,
+                                 long long nnz, const int* old_of_new, int* src, int* dst,
+                                 cudaStream_t st) {
+    if (nnz <= 0) return cudaSuccess;
+    const int g = grid_for(nnz, 256);
+    if (off_bytes == 8)
+        k_rl_unmap<<<g, 256, 0, st>>>((const long long*)row_ptr, col, n, nnz, old_of_new, src, dst);
+    else
+        k_rl_unmap<<<g, 256, 0, st>>>((const int*)row_ptr, col, n, nnz, old_of_new, src, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+
 kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const int* dst,
-                            int off_bytes, int sort_mode, cudaStream_t st, DevCsr* out,
-                            std::string* err) {
+                            int off_bytes, int sort_mode, int relabel, cudaStream_t st, DevCsr* out,
+                            int** new_of_old, int** old_of_new, std::string* err) {
+    if (new_of_old) *new_of_old = nullptr;
+    if (old_of_new) *old_of_new = nullptr;
     if (samples > 0x7fffffffLL) {
         *err = "at most 2^31-1 samples per graph";
         return KCORE_ERR_INVALID;
     }
+    if (!new_of_old || !old_of_new) relabel = -1;
     Temp tmp(st);
     uint32_t* cnt = nullptr;
     BuildCtl* bc = nullptr;
@@ -1367,15 +1481,12 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
     KC_TRY(tmp.get(&bc, 1), "build state");
     KC_TRY(tmp.get(&cnt, (size_t)std::max<int64_t>(n, 1)), "counts");
     KC_TRY(cudaMemsetAsync(tmp.base, 0, tmp.used, st), "memset");  // the state and the counts
-    if (samples > 0 && sort_mode > 0)
-        return sorted_build(tmp, n, samples, src, dst, bc, off_bytes, st, out, err);
-    // Automatic choice, for large inputs of average degree >= kSortAutoDegree
-    // only (the others skip the wait): the sorted build when rows of more than
-    // kSmallMax entries hold at least half of the entries, estimated from every
-    // kSortProbe-th sample.  Per-row counting and sorting is cheaper while rows
-    // are short; hub rows make its atomics collide and need the larger sorts.
-    // Either way the cleaned graph is the same.
-    if (sort_mode == 0 && samples >= kSortAutoSamples && 2 * samples >= kSortAutoDegree * n) {
+    // The probe: every kSortProbe-th run of samples counted per row.  It
+    // estimates the share of entries in rows longer than kSmallMax (the
+    // automatic choice of the pipeline and of renumbering) and, for a
+    // renumbered build, the degree order.
+    bool probed = false, heavy = false;
+    auto probe = [&]() -> kcore_status {
         k_count_coo<<<grid_for(samples / kSortProbe + 256, 256), 256, 0, st>>>(src, dst, samples, (int)n,
                                                                              cnt, bc, kSortProbe);
         count_launch();
@@ -1390,10 +1501,38 @@ kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const in
             *err = "an edge endpoint or a row offset is out of range";
             return KCORE_ERR_INVALID;
         }
-        if (hbc.entries > 0 && 2 * hbc.heavy >= hbc.entries)
-            return sorted_build(tmp, n, samples, src, dst, bc, off_bytes, st, out, err);
-        KC_TRY(cudaMemsetAsync(cnt, 0, cnt_bytes, st), "memset");
+        probed = true;
+        heavy = hbc.entries > 0 && 2 * hbc.heavy >= hbc.entries;
+        return KCORE_OK;
+    };
+    // Automatic choice, for large inputs of average degree >= kSortAutoDegree
+    // only (the others skip the wait): the sorted build when rows of more than
+    // kSmallMax entries hold at least half of the entries.  Per-row counting
+    // and sorting is cheaper while rows are short; hub rows make its atomics
+    // collide and need the larger sorts.  The same test picks renumbering by
+    // descending degree (relabel 0).  Either way the cleaned graph is the same
+    // up to the numbering.
+    const bool auto_size = samples >= kSortAutoSamples && 2 * samples >= kSortAutoDegree * n;
+    bool use_sorted = samples > 0 && sort_mode > 0;
+    if (samples > 0 && ((sort_mode == 0 && auto_size) || (relabel == 0 && auto_size))) {
+        kcore_status ps = probe();
+        if (ps != KCORE_OK) return ps;
+        if (sort_mode == 0) use_sorted = heavy;
     }
+    int rmode = relabel > 0 ? relabel : (relabel == 0 && probed && heavy ? 1 : 0);
+    if (samples == 0 || n < 2) rmode = 0;
+    if (rmode) {
+        use_sorted = true;  // renumbering is done by the sorted build
+        if (!probed) {
+            kcore_status ps = probe();
+            if (ps != KCORE_OK) return ps;
+        }
+        kcore_status rs = make_renumbering(tmp, n, cnt, rmode == 1 ? 1 : 0, st, new_of_old, old_of_new, err);
+        if (rs != KCORE_OK) return rs;
+        return sorted_build(tmp, n, samples, src, dst, bc, off_bytes, st, out, err, *new_of_old);
+    }
+    if (use_sorted) return sorted_build(tmp, n, samples, src, dst, bc, off_bytes, st, out, err, nullptr);
+    if (probed) KC_TRY(cudaMemsetAsync(cnt, 0, cnt_bytes, st), "memset");
     if (samples > 0) {
         k_count_coo<<<grid_for(samples, 256), 256, 0, st>>>(src, dst, samples, (int)n, cnt, bc, 1);
         count_launch();
@@ -1488,10 +1627,9 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
     KC_TRY(tmp.get(&cnt, (size_t)kTiers * nb), "tier counts");
     KC_TRY(tmp.get(&off, (size_t)kTiers * nb + 1), "tier offsets");
     if (off_bytes == 8)
-        k_tier_count<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, cnt, nb,
-                                          &dout->bad);
+        k_tier_count<<<nb, kTsT, 0, st>>>((const long long*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, dout);
     else
-        k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, &dout->bad);
+        k_tier_count<<<nb, kTsT, 0, st>>>((const int*)row_ptr, (int)n, t_lo, t_hi, cnt, nb, dout);
     count_launch();
     KC_TRY(cudaGetLastError(), "tier count");
     KC_TRY(exclusive_scan(ReadU32{cnt}, (long long)kTiers * nb, off, true, st, &tmp), "tier scan");
@@ -1507,6 +1645,15 @@ kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo,
     count_launch();
     KC_TRY(cudaGetLastError(), "tier out");
     return KCORE_OK;
+}
+cudaError_t launch_relabel_start(const int* start, const int* frontier, long long nf, long long n,
+                                 const int* old_of_new, const int* new_of_old, int* start2,
+                                 int* frontier2, cudaStream_t st) {
+    const long long items = std::max<long long>({n, nf, 1LL});
+    k_rl_start<<<grid_for(items, 256), 256, 0, st>>>(start, frontier, nf, n, old_of_new, new_of_old, start2,
+                                                     frontier2);
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace kc

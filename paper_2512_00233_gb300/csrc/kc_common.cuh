@@ -89,6 +89,7 @@ struct SweepArgs {
     const uint32_t* est0;            // a2: est <- est0, F_0 = every vertex, with init_cnt per tier
     unsigned init_cnt[kTiers];
     int* out;                        // a6: out[v] = est[v] (coreness), at the end of the run
+    const int* perm;                 // relabeled graph: out[v] = est[perm[v]], v in the caller's ids
 };
 
 // Launch the persistent sweep kernel (cooperative launch).  `grid` 0 picks the
@@ -114,11 +115,15 @@ struct DevCsr {
 
 // Raw samples (device) -> clean CSR (device, allocated here).  sort_mode 1:
 // the sorted build (one radix sort of all entries); -1: rows counted,
-// scattered and sorted one by one; 0: chosen from the row sizes.  Returns a
-// kcore_status; on error *err names the problem.
+// scattered and sorted one by one; 0: chosen from the row sizes.  relabel
+// (kcore_options.relabel; -1 when new_of_old / old_of_new are null): when the
+// build renumbers the vertices by degree, the CSR is in the new ids (rows
+// sorted by them) and *new_of_old / *old_of_new (n each, allocated here) give
+// the numbering; otherwise both stay null.  Returns a kcore_status; on error
+// *err names the problem.
 kcore_status clean_from_coo(int64_t n, int64_t samples, const int* src, const int* dst,
-                            int off_bytes, int sort_mode, cudaStream_t st, DevCsr* out,
-                            std::string* err);
+                            int off_bytes, int sort_mode, int relabel, cudaStream_t st, DevCsr* out,
+                            int** new_of_old, int** old_of_new, std::string* err);
 kcore_status clean_from_csr(int64_t n, const void* row_ptr, int in_off_bytes, const int* col,
                             int64_t nnz, int off_bytes, cudaStream_t st, DevCsr* out,
                             std::string* err);
@@ -139,6 +144,18 @@ struct TierOut {
 kcore_status tier_split(int64_t n, const void* row_ptr, int off_bytes, int t_lo, int t_hi,
                         uint32_t* est0, int* init_list, TierOut* dout, cudaStream_t st,
                         std::string* err);
+
+// The entries of a renumbered CSR as samples in the caller's ids: src[p] the
+// old id of entry p's row, dst[p] the old id of its column (nnz each).
+cudaError_t launch_relabel_unmap(const void* row_ptr, int off_bytes, const int* col, long long n,
+                                 long long nnz, const int* old_of_new, int* src, int* dst,
+                                 cudaStream_t st);
+
+// start2[i] = start[old_of_new[i]] (i < n); frontier2[j] = new_of_old[frontier[j]]
+// for ids in [0, n) (others copied as they are, so that they are still refused).
+cudaError_t launch_relabel_start(const int* start, const int* frontier, long long nf, long long n,
+                                 const int* old_of_new, const int* new_of_old, int* start2,
+                                 int* frontier2, cudaStream_t st);
 
 // Exclusive scan helper (device), out has N+1 entries when total_slot.
 cudaError_t scan_u32_to_u64(const uint32_t* in, unsigned long long* out, long long N,

@@ -500,7 +500,8 @@ kcore_status admit(kcore_batch* b, bool* fatal) {
     }
     if (e != cudaSuccess) s = cuda_status(e, "batch admission copy");
     if (s == KCORE_OK) {
-        s = clean_from_coo(nu, samples, dsrc, dst_, 8, b->opt.sweep.build_sort, st, &csr, &err);
+        s = clean_from_coo(nu, samples, dsrc, dst_, 8, b->opt.sweep.build_sort, -1, st, &csr, nullptr,
+                           nullptr, &err);
         if (s != KCORE_OK) set_error(err);
     }
     if (s == KCORE_OK) {  // the cleaned size

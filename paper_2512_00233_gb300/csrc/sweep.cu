@@ -1076,7 +1076,8 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
     // a6 inside the launch: every CTA copies its share of the final estimates
     auto write_out = [&]() {
         if (a.out)
-            for (long long v = gtid; v < a.n; v += gstride) a.out[v] = (int)(est_load(a.est + v) & kEstMask);
+            for (long long v = gtid; v < a.n; v += gstride)
+                a.out[v] = (int)(est_load(a.est + (a.perm ? __ldg(a.perm + v) : (int)v)) & kEstMask);
     };
     // a2 inside the launch: estimates from the degrees, F_0 = every vertex
     if (a.est0) {
