@@ -81,10 +81,13 @@ def parse():
     ap.add_argument("--graph", dest="graph", action="store_true", default=None,
                     help="runs replay a captured CUDA graph (KCORE_GRAPH; default for rmat24_planted)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--options", default=None,
+                    help='kcore_options fields as JSON (e.g. \'{"relabel": 2, "block": 256}\'); '
+                         'replaces the autotuner')
     a = ap.parse_args()
     heavy = a.workload == "rmat24_planted"
     if a.autotune is None:
-        a.autotune = heavy
+        a.autotune = heavy and a.options is None
     if a.graph is None:
         a.graph = heavy
     return a
@@ -381,7 +384,10 @@ def run_ours(args):
     opts = None
     tuned = None
     t_tune = 0.0
-    if args.autotune:
+    if args.options:
+        tuned = json.loads(args.options)
+        opts = K.default_options(**tuned)
+    elif args.autotune:
         # the vertex numbering first (fixed when a graph is made), then the
         # sweep knobs on a graph with that numbering
         from paper_2512_00233_gb300 import autotune
