@@ -73,6 +73,9 @@ def parse():
                     help="page-locked host staging of the batch engine (stream)")
     ap.add_argument("--arena-gib", type=int, default=16)
     ap.add_argument("--chunk-sweeps", type=int, default=16)
+    ap.add_argument("--no-serve-tune", action="store_true",
+                    help="stream: skip the batch engine's knob tuning on the first graphs")
+    ap.add_argument("--serve-tune-graphs", type=int, default=2000)
     ap.add_argument("--check-workers", type=int, default=12,
                     help="oracle processes that check every stream result")
     ap.add_argument("--autotune", dest="autotune", action="store_true", default=None,
@@ -671,6 +674,22 @@ def run_stream(args, K, torch, after_timed=None):
     t_gen = time.perf_counter() - t0
     opts = K.default_serve_options(mem_budget=args.arena_gib << 30, chunk_sweeps=args.chunk_sweeps,
                                    host_staging=args.host_staging_gib << 30)
+    serve_tuned, t_tune = None, 0.0
+    if not args.no_serve_tune:
+        # the engine's knobs tuned on the first graphs of the stream (saturated
+        # graphs/s; every candidate's results checked against the first's)
+        import copy
+
+        from paper_2512_00233_gb300 import autotune
+        t0 = time.perf_counter()
+        base = copy.copy(opts)
+        base.host_staging = min(opts.host_staging, 2 << 30)
+        best, _ = autotune.autotune_serve(graphs[:min(G, args.serve_tune_graphs)], base, reps=1)
+        opts.chunk_sweeps = best.chunk_sweeps
+        opts.sweep = best.sweep
+        t_tune = time.perf_counter() - t0
+        serve_tuned = {"chunk_sweeps": best.chunk_sweeps,
+                       **{k: getattr(best.sweep, k) for k in autotune.SERVE_SPACE if k != "chunk_sweeps"}}
     serve_one_launch(K, graphs[:3], None)            # warm-up
     runs = {}
     hashes = {}
@@ -730,7 +749,11 @@ def run_stream(args, K, torch, after_timed=None):
                     "ER avg degree 8 / R-MAT 8n samples / damaged grid)" % G,
         "graphs": G, "m_total": m_total, "metric": "graphs/s and p50/p99 latency",
         "arena_gib": args.arena_gib, "host_staging_gib": args.host_staging_gib,
-        "chunk_sweeps": args.chunk_sweeps,
+        "chunk_sweeps": opts.chunk_sweeps,
+        "serve_options": serve_tuned or "library defaults",
+        "serve_tune": (f"coordinate descent over {sorted(['chunk_sweeps', 'block', 't_hi', 'med_chunk'])} "
+                       f"on the first {min(G, args.serve_tune_graphs)} graphs, {t_tune:.1f} s")
+        if serve_tuned else None,
         "latency": "arrival (time.perf_counter before the request is handed in) to the result "
                    "on the host; one launch per graph: coreness in the caller's buffer; batched: "
                    "the engine's result-ready time on the same monotonic clock",

@@ -11,6 +11,11 @@ Every candidate run is checked to give the same coreness as the first.
 Results are cached in a JSON file keyed by coarse degree statistics (log2 of
 n, of the average degree and of the maximum degree), so graphs of the same
 shape reuse a tuning: `tuned_options(graph)`.
+
+`autotune_serve` tunes the batch engine the same way on a sample of a graph
+stream: sweeps per persistent launch and the sweep knobs of the arena, by the
+saturated throughput (graphs/s) of the sample, every result checked against
+the first candidate's.
 """
 from __future__ import annotations
 
@@ -125,3 +130,71 @@ def tuned_options(graph: Graph, cache: str = DEFAULT_CACHE) -> Options | None:
         data = json.load(f)
     e = data.get(shape_key(graph))
     return default_options(**e["options"]) if e else None
+
+
+SERVE_SPACE = {
+    "chunk_sweeps": [4, 8, 16, 32, 64],
+    "block": [256, 512],
+    "t_hi": [256, 1024, 2048],
+    "med_chunk": [1, 4, 16],
+}
+
+
+def _serve_rate(graphs, opts, reps: int, check=None):
+    """Median saturated graphs/s of the batch engine on `graphs` (every one
+    submitted at once, then polled), and the results of the last repetition."""
+    import time
+
+    from . import BatchEngine
+    rates, res = [], None
+    for _ in range(reps):
+        with BatchEngine(opts) as eng:
+            t0 = time.perf_counter()
+            tickets = [eng.submit_coo(g.n, g.src, g.dst) for g in graphs]
+            res = [eng.poll(t, g.n, timeout_us=-1)[1] for g, t in zip(graphs, tickets)]
+            rates.append(len(graphs) / (time.perf_counter() - t0))
+    if check is not None:
+        for a, b in zip(res, check):
+            assert a is not None and np.array_equal(a, b), "serve candidate changed a result"
+    return statistics.median(rates), res
+
+
+def autotune_serve(graphs, base, reps: int = 2, passes: int = 1, space: dict | None = None,
+                   verbose: bool = False):
+    """Coordinate descent over SERVE_SPACE for the batch engine on a stream
+    sample.  `base`: a ServeOptions to start from (mem_budget, staging, ...).
+    Returns (best ServeOptions, trials [(knob, value, graphs/s)])."""
+    import copy
+
+    space = space or SERVE_SPACE
+
+    def make(knobs):
+        o = copy.copy(base)
+        sw = copy.copy(base.sweep)
+        for k, v in knobs.items():
+            if k == "chunk_sweeps":
+                o.chunk_sweeps = v
+            else:
+                setattr(sw, k, v)
+        o.sweep = sw
+        return o
+
+    best = {"chunk_sweeps": base.chunk_sweeps}
+    best.update({k: getattr(base.sweep, k) for k in space if k != "chunk_sweeps"})
+    best_rate, ref = _serve_rate(graphs, make(best), reps)
+    trials = [("base", None, best_rate)]
+    for _ in range(passes):
+        for knob, values in space.items():
+            for val in values:
+                if val == best[knob]:
+                    continue
+                cand = dict(best, **{knob: val})
+                if cand.get("t_hi", 2048) < base.sweep.t_lo:
+                    continue
+                rate, _ = _serve_rate(graphs, make(cand), reps, ref)
+                trials.append((knob, val, rate))
+                if verbose:
+                    print(f"autotune_serve {knob}={val}: {rate:.0f} graphs/s (best {best_rate:.0f})")
+                if rate > best_rate:
+                    best, best_rate = cand, rate
+    return make(best), trials

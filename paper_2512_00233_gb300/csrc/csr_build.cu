@@ -1058,24 +1058,50 @@ __global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int
 // and column bits, then repeats dropped while col_idx and the row counts are
 // written.  No per-row atomics on hot rows and no per-row sorts.  (Making the
 // keys inside the first radix pass instead was slower.)
+// Four samples per thread per round, their loads (and, when renumbering, the
+// gathers of their new ids) issued before any is used.
+constexpr int kSbU = 4;
+
 __global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst, long long S,
                           int n, ulonglong2* __restrict__ keys, BuildCtl* bc,
                           const int* __restrict__ remap) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
-         i += (long long)gridDim.x * blockDim.x) {
-        int s = src[i], d = dst[i];
-        ulonglong2 k = make_ulonglong2(kNoKey, kNoKey);
-        if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n) {
-            bc->bad = 1;
-        } else if (s != d) {
-            if (remap) {
-                s = __ldg(remap + s);
-                d = __ldg(remap + d);
-            }
-            k.x = ((unsigned long long)(unsigned)s << 32) | (unsigned)d;
-            k.y = ((unsigned long long)(unsigned)d << 32) | (unsigned)s;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < S; i0 += kSbU * stride) {
+        int s[kSbU], d[kSbU];
+        bool ok[kSbU];
+#pragma unroll
+        for (int r = 0; r < kSbU; r++) {
+            const long long i = i0 + r * stride;
+            s[r] = i < S ? src[i] : 0;
+            d[r] = i < S ? dst[i] : 0;
         }
-        keys[i] = k;
+#pragma unroll
+        for (int r = 0; r < kSbU; r++) {
+            const long long i = i0 + r * stride;
+            const bool in = (unsigned)s[r] < (unsigned)n && (unsigned)d[r] < (unsigned)n;
+            if (i < S && !in) bc->bad = 1;
+            ok[r] = i < S && in && s[r] != d[r];
+        }
+        if (remap) {
+#pragma unroll
+            for (int r = 0; r < kSbU; r++) {
+                if (ok[r]) {
+                    s[r] = __ldg(remap + s[r]);
+                    d[r] = __ldg(remap + d[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kSbU; r++) {
+            const long long i = i0 + r * stride;
+            if (i >= S) continue;
+            ulonglong2 k = make_ulonglong2(kNoKey, kNoKey);
+            if (ok[r]) {
+                k.x = ((unsigned long long)(unsigned)s[r] << 32) | (unsigned)d[r];
+                k.y = ((unsigned long long)(unsigned)d[r] << 32) | (unsigned)s[r];
+            }
+            keys[i] = k;
+        }
     }
 }
 
@@ -1101,34 +1127,60 @@ __global__ void __launch_bounds__(kRsT) k_sb_count(const unsigned long long* __r
 
 // col_idx[position among distinct keys] = column; ucnt[row] += distinct keys
 // (sorted keys: a warp's lanes share one or two rows, one add per row).
+// Writes the tile's distinct keys' columns in order and adds each row's count.
+// All kRsKpt rounds' keys are loaded and judged first; one barrier then makes
+// the per-round, per-warp counts visible, and each key's rank in the tile is
+// the count of the rounds before it, of the warps before it in its round, and
+// of the lanes before it in its warp.
 __global__ void __launch_bounds__(kRsT) k_sb_emit(const unsigned long long* __restrict__ keys,
                                                   long long N, const uint32_t* __restrict__ toff,
                                                   int* __restrict__ col,
                                                   uint32_t* __restrict__ ucnt) {
-    __shared__ uint32_t wsum[kRsWarps];
+    __shared__ uint32_t cnt[kRsKpt][kRsWarps];
+    __shared__ uint32_t rbase[kRsKpt];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const long long base = (long long)blockIdx.x * kRsTile;
-    uint32_t run = toff[blockIdx.x];
+    unsigned long long k[kRsKpt];
+    uint32_t firsts = 0;
+#pragma unroll
     for (int i = 0; i < kRsKpt; i++) {
         const long long idx = base + (long long)i * kRsT + threadIdx.x;
-        const bool f = idx < N && sb_first(keys, idx);
-        const unsigned m = __ballot_sync(kFull, f);
-        if (lane == 0) wsum[w] = (uint32_t)__popc(m);
-        __syncthreads();
-        uint32_t before = 0, all = 0;
+        k[i] = idx < N ? keys[idx] : kNoKey;
+    }
 #pragma unroll
-        for (int ww = 0; ww < kRsWarps; ww++) {
-            const uint32_t c = wsum[ww];
-            before += ww < w ? c : 0u;
-            all += c;
-        }
-        __syncthreads();
-        const unsigned long long k = f ? keys[idx] : 0ull;
-        const unsigned row = (unsigned)(k >> 32);
-        if (f) col[run + before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (int)(unsigned)k;
+    for (int i = 0; i < kRsKpt; i++) {
+        const long long idx = base + (long long)i * kRsT + threadIdx.x;
+        // the key before this one: the previous lane's, or the last of the
+        // previous round / tile
+        unsigned long long prev = __shfl_up_sync(kFull, k[i], 1);
+        if (lane == 0) prev = idx > 0 ? keys[idx - 1] : ~k[i];
+        const bool f = idx < N && k[i] != kNoKey && k[i] != prev;
+        firsts |= (uint32_t)f << i;
+        const unsigned m = __ballot_sync(kFull, f);
+        if (lane == 0) cnt[i][w] = (uint32_t)__popc(m);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRsKpt) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRsWarps; ww++) t += cnt[threadIdx.x][ww];
+        rbase[threadIdx.x] = t;
+    }
+    __syncthreads();
+    uint32_t run = toff[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kRsKpt; i++) {
+        const bool f = (firsts >> i) & 1u;
+        const unsigned m = __ballot_sync(kFull, f);
+        uint32_t before = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRsWarps; ww++) before += ww < w ? cnt[i][ww] : 0u;
+        const unsigned row = (unsigned)(k[i] >> 32);
+        if (f) col[run + before + (uint32_t)__popc(m & lt)] = (int)(unsigned)k[i];
         const unsigned peers = __match_any_sync(kFull, f ? row : 0xffffffffu);
-        if (f && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&ucnt[row], (uint32_t)__popc(peers));
-        run += all;
+        if (f && (peers & lt) == 0) atomicAdd(&ucnt[row], (uint32_t)__popc(peers));
+        run += rbase[i];
     }
 }
 
