@@ -125,12 +125,26 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     return v;
 }
 
-// Refined rule (asynchronous) for a neighbour v read as x, h < x, while u
-// goes from k to h: push if x <= k or v may still be evaluating (bit set);
-// otherwise decide on v's final value, read after the bit.
-__device__ __forceinline__ bool refined_push(const Sweep& S, int h, int k, int v, int x) {
+// A thread-tier vertex never clears its own membership bit (done marks are
+// made by the warp and CTA tiers only), so its bit in F_s does not change
+// during sweep s: a plain read of it is exact, and a thread-tier neighbour
+// whose bit is clear is not evaluated in this sweep, so the value already
+// read is its final one.  Only warp- and CTA-tier neighbours need the
+// acquire read and the second read of their estimate.
+__device__ __forceinline__ uint32_t member_word(const Sweep& S, int v, uint32_t tier) {
+    return tier == 0 ? __ldcg(S.bmc + (v >> 5)) : ld_acquire(S.bmc + (v >> 5));
+}
+
+// Refined rule (asynchronous) for a neighbour v read as x (tier bits in xw),
+// h < x, while u goes from k to h: push if x <= k or v may still be
+// evaluating (bit set); otherwise decide on v's final value: x itself for a
+// thread-tier v, else read again after the bit.
+__device__ __forceinline__ bool refined_push(const Sweep& S, int h, int k, int v, uint32_t xw) {
+    const int x = (int)(xw & kEstMask);
     if (x <= k) return true;
-    if ((ld_acquire(S.bmc + (v >> 5)) >> (v & 31)) & 1u) return true;
+    const uint32_t tier = xw >> kEstBits;
+    if ((member_word(S, v, tier) >> (v & 31)) & 1u) return true;
+    if (tier == 0) return false;  // x > k is its final value
     const int x2 = (int)(est_load(S.a->est + v) & kEstMask);
     return h < x2 && x2 <= k;
 }
@@ -249,11 +263,16 @@ __device__ __forceinline__ void warp_push_n(const Sweep& S, WarpQ& Q, uint32_t c
         for (int j = 0; j < N; j++)
             if (((cand >> j) & 1u) && (int)(xw[j] & kEstMask) > k) chk |= 1u << j;
 #pragma unroll
-        for (int j = 0; j < N; j++) word[j] = ((chk >> j) & 1u) ? ld_acquire(S.bmc + (vs[j] >> 5)) : 0u;
+        for (int j = 0; j < N; j++)
+            word[j] = ((chk >> j) & 1u) ? member_word(S, vs[j], xw[j] >> kEstBits) : 0u;
         uint32_t again = 0;
 #pragma unroll
-        for (int j = 0; j < N; j++)
-            if (((chk >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) again |= 1u << j;
+        for (int j = 0; j < N; j++) {
+            if (((chk >> j) & 1u) && !((word[j] >> (vs[j] & 31)) & 1u)) {
+                if ((xw[j] >> kEstBits) == 0) cand &= ~(1u << j);  // thread tier: x > k is final
+                else again |= 1u << j;
+            }
+        }
         if (again) {
 #pragma unroll
             for (int j = 0; j < N; j++) word[j] = ((again >> j) & 1u) ? est_load(S.a->est + vs[j]) : 0u;
@@ -462,15 +481,19 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
             pv[c] = cv[c];
             if (cv[c] >= 0 && ch && x > ho) {
                 cand |= 1u << c;
-                word[c] = (a.refined && x > ko) ? ld_acquire(S.bmc + (cv[c] >> 5)) : 0xffffffffu;
+                word[c] = (a.refined && x > ko) ? member_word(S, cv[c], cx[c] >> kEstBits) : 0xffffffffu;
             } else {
                 word[c] = 0xffffffffu;
             }
         }
         uint32_t again = 0;
 #pragma unroll
-        for (int c = 0; c < kLowCache; c++)
-            if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) again |= 1u << c;
+        for (int c = 0; c < kLowCache; c++) {
+            if (((cand >> c) & 1u) && !((word[c] >> (pv[c] & 31)) & 1u)) {
+                if ((cx[c] >> kEstBits) == 0) cand &= ~(1u << c);  // thread tier: x > k is final
+                else again |= 1u << c;
+            }
+        }
         if (__any_sync(kFull, again != 0)) {  // refined rule, v done or never in F_s: its final value decides
 #pragma unroll
             for (int c = 0; c < kLowCache; c++)
@@ -507,7 +530,7 @@ __device__ __forceinline__ void low_warp(const Sweep& S, WarpQ& Q, const Off* __
             v = __ldg(a.col + bo + (g - eo));
             xw = est_load(a.est + v);
             const int x = (int)(xw & kEstMask);
-            want = x > ho && (!a.refined || refined_push(S, ho, ko, v, x));
+            want = x > ho && (!a.refined || refined_push(S, ho, ko, v, xw));
         }
         warp_push(S, Q, want, v, xw >> kEstBits, acc);
     }
