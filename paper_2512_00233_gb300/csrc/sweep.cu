@@ -609,15 +609,22 @@ __device__ __forceinline__ void med_vertex(const Sweep& S, WarpQ& Q, int u, long
 // neighbour staged above k is gathered again for the refined test.
 constexpr int kMedU = 4;
 constexpr int kMedSlice = kMedBig / 2;  // words per warp
+constexpr int kMedWin = 32;             // exact counts kept for [k - kMedWin, k - 1]
 constexpr uint32_t kStageVal = 0x0fffu;   // value bits of a staged word
 constexpr int kStageTier = 14;            // tier bits of a staged word
 
 __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, int u, long long b, int d,
-                                               uint32_t w, uint32_t* slice, Acc& acc) {
+                                               uint32_t w, uint32_t* slice, uint32_t* whist, Acc& acc) {
     const SweepArgs& a = *S.a;
     const int lane = threadIdx.x & 31;
     uint16_t* sx = (uint16_t*)slice;
     const int k = (int)(w & kEstMask);
+    // values in the window [wl, k - 1] are also counted exactly in pass 1, so
+    // that a vertex whose new estimate lands there (the usual case: the
+    // estimates drop by a few per evaluation) needs no bisection
+    const int wl = k > kMedWin ? k - kMedWin : 0;
+    whist[lane] = 0;
+    __syncwarp();
     if (lane == 0) {
         acc.evaluated += 1;
         acc.degsum += (unsigned)d;
@@ -648,6 +655,7 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, int u, 
                 c += x >= k ? 1 : 0;
                 const uint32_t y = (uint32_t)(x <= k ? x : k + 1);
                 sx[j0 + r * 32 + lane] = (uint16_t)(y | ((xw[r] >> kEstBits) << kStageTier));
+                if (x >= wl && x < k) atomicAdd(&whist[x - wl], 1u);
             }
         }
         ck += (int)__reduce_add_sync(kFull, (unsigned)c);
@@ -663,12 +671,30 @@ __device__ __forceinline__ void med_big_vertex(const Sweep& S, WarpQ& Q, int u, 
         __syncwarp();
         return;
     }
+    // h from the window: lane l stands for t = wl + l, with
+    // #{y >= t} = ck + the window counts of bins >= l (a suffix sum); the
+    // predicate #{y >= t} >= t holds for a prefix of t, so h is the last lane
+    // where it holds, if any
+    __syncwarp();
+    uint32_t sfx = whist[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(kFull, sfx, o);
+        if (lane + o < 32) sfx += t;
+    }
+    const int tw = wl + lane;
+    const unsigned inwin = __ballot_sync(kFull, tw < k && (int)(sfx + (uint32_t)ck) >= tw);
     const int padded = (d + 255) & ~255;  // whole 16-byte reads for every lane
     for (int j = d + lane; j < padded; j += 32) sx[j] = 0;
     __syncwarp();
     const uint4* sv = (const uint4*)slice;
     const int nv = padded >> 8;  // 16-byte reads per lane
     int lo = 0, hi = k - 1;      // count(y >= 0) = d >= 0 holds; h < k
+    if (inwin) {
+        lo = hi = wl + (31 - __clz((int)inwin));
+    } else {
+        hi = wl - 1;             // below the window (wl > 0 here: t = 0 always holds)
+    }
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         const uint32_t mid2 = (uint32_t)mid * 0x00010001u;
@@ -1064,7 +1090,8 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
     // and the thread tier's per-warp counts (sizes: sweep_smem_bytes).
     extern __shared__ __align__(16) uint32_t s_dyn[];
     int* s_wbuf = (int*)s_dyn;
-    uint32_t* s_pool = s_dyn + (blockDim.x >> 5) * kWCap;
+    uint32_t* s_whist = s_dyn + (blockDim.x >> 5) * kWCap;  // warp tier: window counts
+    uint32_t* s_pool = s_whist + (blockDim.x >> 5) * kMedWin;
     __shared__ uint32_t s_cls[32];
     __shared__ uint32_t s_cnt[3 * 32];
     __shared__ uint32_t s_hub[4];
@@ -1326,7 +1353,8 @@ __global__ void __launch_bounds__(kMaxBlock, kMinBlocks) k_sweep(const SweepArgs
                         const int dt = (int)(__shfl_sync(kFull, re, (int)t) - bt);
                         const uint32_t wt = __shfl_sync(kFull, w, (int)t);
                         if (dt <= 32 * kMedR) med_vertex<kMedR>(S, Q, ut, bt, dt, wt, acc);
-                        else med_big_vertex(S, Q, ut, bt, dt, wt, s_pool + wid * kMedSlice, acc);
+                        else med_big_vertex(S, Q, ut, bt, dt, wt, s_pool + wid * kMedSlice,
+                                            s_whist + wid * kMedWin, acc);
                     }
                 }
             });
@@ -1443,7 +1471,7 @@ size_t sweep_smem_bytes(int block) {
     const size_t nw = (size_t)block / 32;
     const size_t pool = std::max<size_t>({(size_t)kLogWords * block + kHubBins, nw * kMedSlice});
     static_assert((16 / 4) * 32 <= kMedSlice, "thread tier counts exceed a warp's slice");
-    return sizeof(uint32_t) * (nw * kWCap + pool);
+    return sizeof(uint32_t) * (nw * (kWCap + kMedWin) + pool);
 }
 
 cudaError_t prepare(const void* fn, int block, int* per_sm) {
