@@ -773,87 +773,127 @@ __global__ void __launch_bounds__(kRsT) k_rs_hist(In keys, long long N, int shif
     hist[(long long)threadIdx.x * nt + blockIdx.x] = c;
 }
 
-// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes in
-// `valid` (one ballot per digit bit).
-__device__ __forceinline__ unsigned digit_peers(unsigned d, unsigned valid) {
-    unsigned peers = valid;
-#pragma unroll
-    for (int b = 0; b < 8; b++) {
-        const bool bit = (d >> b) & 1u;
-        const unsigned m = __ballot_sync(kFull, bit);
-        peers &= bit ? m : ~m;
-    }
-    return peers;
+// Byte B of a 64-bit key (the digit of the pass at shift 8B).
+template <int B>
+__device__ __forceinline__ unsigned key_byte(unsigned long long k) {
+    const uint32_t w = B < 4 ? (uint32_t)k : (uint32_t)(k >> 32);
+    return __byte_perm(w, 0u, 0x4440u + (unsigned)(B & 3));
 }
 
-// Warp w owns keys [w*512, w*512 + 512) of the tile and walks them in 16
-// rounds of 32; ranks follow (warp, round, lane), which is input order.
-template <typename In>
-__global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(In in, unsigned long long* __restrict__ out,
-                                                        long long N, int shift,
-                                                        const uint32_t* __restrict__ off,
-                                                        long long nt) {
-    __shared__ unsigned long long sk[kRsTile];
-    __shared__ uint32_t wc[kRsWarps][256];
-    __shared__ uint32_t dstart[256], goff[256];
+// One tile.  Warp w owns keys [w*512, w*512 + 512) of the tile and walks them
+// in 16 rounds of 32; ranks follow (warp, round, lane), which is input order.
+// The lanes holding the same digit in a round are found through a per-warp
+// table of 256 lane masks in shared memory: every lane ORs its bit into its
+// digit's word and reads the word back (two tables used in alternate rounds,
+// a word cleared after it is read, so that each is clear again two rounds
+// later).  The tables live in the staging area, which is only written after
+// the ranking.  FULL: the tile holds kRsTile keys (no bounds checks).
+template <typename In, int B, bool FULL>
+__device__ __forceinline__ void scatter_tile(const In& in, unsigned long long* __restrict__ out,
+                                             long long N, long long tile0, uint32_t my_goff,
+                                             unsigned long long* sk, uint32_t (*wc)[256],
+                                             uint32_t* gd) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const long long tile0 = (long long)blockIdx.x * kRsTile;
+    const unsigned lt_mask = (1u << lane) - 1u, my_bit = 1u << lane;
     const long long base = tile0 + (long long)w * (32 * kRsKpt);
     unsigned long long key[kRsKpt];
-    uint32_t rank[kRsKpt];
-    // the tile's keys and its run starts are fetched together, before any wait
+    uint32_t rank[kRsKpt / 2];  // two 16-bit ranks (< kRsTile) per word
+    // the tile's keys are fetched before any wait
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
         const long long idx = base + r * 32 + lane;
-        key[r] = idx < N ? in(idx) : 0ull;
+        key[r] = (FULL || idx < N) ? in(idx) : 0ull;
     }
-    const uint32_t my_goff = off[(long long)tid * nt + blockIdx.x];
-    for (int i = tid; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
+    uint32_t* peer_tab = reinterpret_cast<uint32_t*>(sk) + w * 512;  // two 256-word tables
+    // clear the mask tables and the counts
+    {
+        uint4* z = reinterpret_cast<uint4*>(sk);
+        for (int i = tid; i < kRsWarps * 512 / 4; i += kRsT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
-        const bool valid = base + r * 32 + lane < N;
-        const unsigned d = (unsigned)(key[r] >> shift) & 255u;
-        const unsigned peers = digit_peers(d, __ballot_sync(kFull, valid));
+        const bool valid = FULL || base + r * 32 + lane < N;
+        const unsigned d = key_byte<B>(key[r]);
+        uint32_t* m = peer_tab + (r & 1) * 256 + d;
+        if (valid) atomicOr(m, my_bit);
+        __syncwarp();
+        const unsigned peers = valid ? *m : 0u;
         const unsigned lower = peers & lt_mask;
         const uint32_t before = valid ? wc[w][d] : 0u;
         __syncwarp();
         if (valid && lower == 0) wc[w][d] = before + (uint32_t)__popc(peers);
-        __syncwarp();
-        rank[r] = before + (uint32_t)__popc(lower);
+        if (valid) *m = 0u;  // clear for round r + 2
+        const uint32_t rk = before + (uint32_t)__popc(lower);
+        if (r & 1) rank[r >> 1] |= rk << 16;
+        else rank[r >> 1] = rk;
     }
     __syncthreads();
-    // thread tid = digit: exclusive prefix over the warps, then over the digits
+    // thread tid = digit: exclusive prefix over the warps, then over the
+    // digits; the warps' counts become their staging bases
     uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kRsWarps; ww++) run += wc[ww][tid];
+    unsigned long long tot;
+    const uint32_t ds = (uint32_t)block_excl_scan(run, &tot);
+    uint32_t acc = ds;
 #pragma unroll
     for (int ww = 0; ww < kRsWarps; ww++) {
         const uint32_t c = wc[ww][tid];
-        wc[ww][tid] = run;
-        run += c;
+        wc[ww][tid] = acc;
+        acc += c;
     }
-    unsigned long long tot;
-    dstart[tid] = (uint32_t)block_excl_scan(run, &tot);
-    goff[tid] = my_goff;
+    gd[tid] = my_goff - ds;  // output index of staged position p: gd[digit] + p
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
-        if (base + r * 32 + lane < N) {
-            const unsigned d = (unsigned)(key[r] >> shift) & 255u;
-            sk[dstart[d] + wc[w][d] + rank[r]] = key[r];
+        if (FULL || base + r * 32 + lane < N) {
+            const unsigned d = key_byte<B>(key[r]);
+            sk[wc[w][d] + ((rank[r >> 1] >> (16 * (r & 1))) & 0xffffu)] = key[r];
         }
     }
     __syncthreads();
-    const int cnt = (int)min((long long)kRsTile, N - tile0);
+    const int cnt = FULL ? kRsTile : (int)min((long long)kRsTile, N - tile0);
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
         const int p = r * kRsT + tid;
-        if (p < cnt) {
+        if (FULL || p < cnt) {
             const unsigned long long k = sk[p];
-            const unsigned d = (unsigned)(k >> shift) & 255u;
-            out[(long long)goff[d] + (uint32_t)(p - (int)dstart[d])] = k;
+            out[(long long)(uint32_t)(gd[key_byte<B>(k)] + (uint32_t)p)] = k;
         }
     }
+}
+
+template <typename In, int B>
+__global__ void __launch_bounds__(kRsT, 3) k_rs_scatter(In in, unsigned long long* __restrict__ out,
+                                                        long long N, const uint32_t* __restrict__ off,
+                                                        long long nt) {
+    __shared__ __align__(16) unsigned long long sk[kRsTile];
+    __shared__ uint32_t wc[kRsWarps][256];
+    __shared__ uint32_t gd[256];
+    const long long tile0 = (long long)blockIdx.x * kRsTile;
+    const uint32_t my_goff = off[(long long)threadIdx.x * nt + blockIdx.x];
+    if (tile0 + kRsTile <= N) scatter_tile<In, B, true>(in, out, N, tile0, my_goff, sk, wc, gd);
+    else scatter_tile<In, B, false>(in, out, N, tile0, my_goff, sk, wc, gd);
+}
+
+template <typename In>
+cudaError_t launch_scatter(int shift, unsigned grid, cudaStream_t st, In in,
+                           unsigned long long* out, long long N, const uint32_t* off, long long nt) {
+    switch (shift) {
+        case 0: k_rs_scatter<In, 0><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 8: k_rs_scatter<In, 1><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 16: k_rs_scatter<In, 2><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 24: k_rs_scatter<In, 3><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 32: k_rs_scatter<In, 4><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 40: k_rs_scatter<In, 5><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 48: k_rs_scatter<In, 6><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        case 56: k_rs_scatter<In, 7><<<grid, kRsT, 0, st>>>(in, out, N, off, nt); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
 }
 
 // Sorts the N keys of `first` by bits [0, lowbits) then [32, 32 + highbits)
@@ -888,11 +928,9 @@ cudaError_t radix_sort(In first, long long N, unsigned long long* buf0, unsigned
         if (e == cudaSuccess) e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st, tmp);
         if (e != cudaSuccess) break;
         if (p == 0)
-            k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(first, out, N, sh, off, nt);
+            e = launch_scatter(sh, (unsigned)nt, st, first, out, N, off, nt);
         else
-            k_rs_scatter<<<(unsigned)nt, kRsT, 0, st>>>(KeyIn{buf[(p - 1) % 2]}, out, N, sh, off, nt);
-        count_launch();
-        e = cudaGetLastError();
+            e = launch_scatter(sh, (unsigned)nt, st, KeyIn{buf[(p - 1) % 2]}, out, N, off, nt);
         *result = out;
     }
     return e;
