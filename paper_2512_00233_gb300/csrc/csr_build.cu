@@ -783,18 +783,20 @@ __device__ __forceinline__ unsigned key_byte(unsigned long long k) {
 // One tile.  Warp w owns keys [w*512, w*512 + 512) of the tile and walks them
 // in 16 rounds of 32; ranks follow (warp, round, lane), which is input order.
 // The lanes holding the same digit in a round are found through a per-warp
-// table of 256 lane masks in shared memory: every lane ORs its bit into its
-// digit's word and reads the word back (two tables used in alternate rounds,
-// a word cleared after it is read, so that each is clear again two rounds
-// later).  The tables live in the staging area, which is only written after
-// the ranking.  FULL: the tile holds kRsTile keys (no bounds checks).
+// table of 256 words in shared memory: every lane writes its lane number into
+// its digit's word and reads the word back; one writer per digit wins, so the
+// number read is a label shared by exactly the lanes of that digit, and five
+// ballots over its bits give the peers (eight would be needed over the digit
+// itself; shared-memory atomics on the table cost more in bank conflicts).
+// The tables live in the staging area, which is only written after the
+// ranking.  FULL: the tile holds kRsTile keys (no bounds checks).
 template <typename In, int B, bool FULL>
 __device__ __forceinline__ void scatter_tile(const In& in, unsigned long long* __restrict__ out,
                                              long long N, long long tile0, uint32_t my_goff,
                                              unsigned long long* sk, uint32_t (*wc)[256],
                                              uint32_t* gd) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u, my_bit = 1u << lane;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const long long base = tile0 + (long long)w * (32 * kRsKpt);
     unsigned long long key[kRsKpt];
     uint32_t rank[kRsKpt / 2];  // two 16-bit ranks (< kRsTile) per word
@@ -804,27 +806,28 @@ __device__ __forceinline__ void scatter_tile(const In& in, unsigned long long* _
         const long long idx = base + r * 32 + lane;
         key[r] = (FULL || idx < N) ? in(idx) : 0ull;
     }
-    uint32_t* peer_tab = reinterpret_cast<uint32_t*>(sk) + w * 512;  // two 256-word tables
-    // clear the mask tables and the counts
-    {
-        uint4* z = reinterpret_cast<uint4*>(sk);
-        for (int i = tid; i < kRsWarps * 512 / 4; i += kRsT) z[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = tid; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
-    }
+    uint32_t* label = reinterpret_cast<uint32_t*>(sk) + w * 256;
+    for (int i = tid; i < kRsWarps * 256; i += kRsT) (&wc[0][0])[i] = 0;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsKpt; r++) {
         const bool valid = FULL || base + r * 32 + lane < N;
         const unsigned d = key_byte<B>(key[r]);
-        uint32_t* m = peer_tab + (r & 1) * 256 + d;
-        if (valid) atomicOr(m, my_bit);
+        if (valid) label[d] = (uint32_t)lane;
         __syncwarp();
-        const unsigned peers = valid ? *m : 0u;
+        const unsigned rep = valid ? label[d] : 0u;
+        unsigned peers = FULL ? kFull : __ballot_sync(kFull, valid);
+#pragma unroll
+        for (int b = 0; b < 5; b++) {
+            const bool bit = (rep >> b) & 1u;
+            const unsigned m = __ballot_sync(kFull, bit);
+            peers &= bit ? m : ~m;
+        }
+        if (!valid) peers = 0u;
         const unsigned lower = peers & lt_mask;
         const uint32_t before = valid ? wc[w][d] : 0u;
         __syncwarp();
         if (valid && lower == 0) wc[w][d] = before + (uint32_t)__popc(peers);
-        if (valid) *m = 0u;  // clear for round r + 2
         const uint32_t rk = before + (uint32_t)__popc(lower);
         if (r & 1) rank[r >> 1] |= rk << 16;
         else rank[r >> 1] = rk;
@@ -903,7 +906,7 @@ cudaError_t launch_scatter(int shift, unsigned grid, cudaStream_t st, In in,
 template <typename In>
 cudaError_t radix_sort(In first, long long N, unsigned long long* buf0, unsigned long long* buf1,
                        int lowbits, int highbits, cudaStream_t st, unsigned long long** result,
-                       Temp* tmp, int* bad) {
+                       Temp* tmp, int* bad, const uint32_t* hist0 = nullptr) {
     const long long nt = (N + kRsTile - 1) / kRsTile;
     uint32_t *hist = nullptr, *off = nullptr;
     cudaError_t e = tmp->get(&hist, (size_t)256 * nt);
@@ -917,15 +920,20 @@ cudaError_t radix_sort(In first, long long N, unsigned long long* buf0, unsigned
     for (size_t p = 0; p < shifts.size() && e == cudaSuccess; p++) {
         const int sh = shifts[p];
         unsigned long long* out = buf[p % 2];
-        if (p == 0) {
-            k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(first, N, sh, hist, nt, bad);
+        const uint32_t* h = hist;
+        if (p == 0 && hist0) {
+            h = hist0;  // counted by the caller while it wrote the keys
         } else {
-            k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(KeyIn{buf[(p - 1) % 2]}, N, sh, hist, nt,
-                                                     (int*)nullptr);
+            if (p == 0) {
+                k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(first, N, sh, hist, nt, bad);
+            } else {
+                k_rs_hist<<<(unsigned)nt, kRsT, 0, st>>>(KeyIn{buf[(p - 1) % 2]}, N, sh, hist, nt,
+                                                         (int*)nullptr);
+            }
+            count_launch();
+            e = cudaGetLastError();
         }
-        count_launch();
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = exclusive_scan(ReadU32{hist}, 256 * nt, off, false, st, tmp);
+        if (e == cudaSuccess) e = exclusive_scan(ReadU32{h}, 256 * nt, off, false, st, tmp);
         if (e != cudaSuccess) break;
         if (p == 0)
             e = launch_scatter(sh, (unsigned)nt, st, first, out, N, off, nt);
@@ -1108,23 +1116,32 @@ __global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int
 constexpr int kSbU = 4;
 
 // One key per sample: its canonical form (min << 32 | max) of the two
-// (renumbered) ends; a loop or a bad id becomes kNoKey.
-__global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst, long long S,
-                          int n, unsigned long long* __restrict__ keys, BuildCtl* bc,
-                          const int* __restrict__ remap) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < S; i0 += kSbU * stride) {
+// (renumbered) ends; a loop or a bad id becomes kNoKey.  A CTA makes one tile
+// of kRsTile keys (the radix sort's tiles) and counts their lowest bytes, the
+// digits of the sort's first pass, into column blockIdx.x of the digit-major
+// count matrix `hist`, which saves that pass its histogram read.
+__global__ void __launch_bounds__(kRsT) k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst,
+                                                  long long S, int n, unsigned long long* __restrict__ keys,
+                                                  BuildCtl* bc, const int* __restrict__ remap,
+                                                  uint32_t* __restrict__ hist, long long nt) {
+    __shared__ uint32_t sh[kRsWarps][256];
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; q++) sh[q][threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRsTile;
+    for (int i0 = 0; i0 < kRsKpt; i0 += kSbU) {
         int s[kSbU], d[kSbU];
         bool ok[kSbU];
 #pragma unroll
         for (int r = 0; r < kSbU; r++) {
-            const long long i = i0 + r * stride;
+            const long long i = base + (long long)(i0 + r) * kRsT + threadIdx.x;
             s[r] = i < S ? src[i] : 0;
             d[r] = i < S ? dst[i] : 0;
         }
 #pragma unroll
         for (int r = 0; r < kSbU; r++) {
-            const long long i = i0 + r * stride;
+            const long long i = base + (long long)(i0 + r) * kRsT + threadIdx.x;
             const bool in = (unsigned)s[r] < (unsigned)n && (unsigned)d[r] < (unsigned)n;
             if (i < S && !in) bc->bad = 1;
             ok[r] = i < S && in && s[r] != d[r];
@@ -1140,12 +1157,19 @@ __global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ d
         }
 #pragma unroll
         for (int r = 0; r < kSbU; r++) {
-            const long long i = i0 + r * stride;
+            const long long i = base + (long long)(i0 + r) * kRsT + threadIdx.x;
             if (i >= S) continue;
             const unsigned lo = (unsigned)min(s[r], d[r]), hi = (unsigned)max(s[r], d[r]);
-            keys[i] = ok[r] ? ((unsigned long long)lo << 32) | hi : kNoKey;
+            const unsigned long long k = ok[r] ? ((unsigned long long)lo << 32) | hi : kNoKey;
+            keys[i] = k;
+            atomicAdd(&sh[w][(unsigned)k & 255u], 1u);
         }
     }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; q++) c += sh[q][threadIdx.x];
+    hist[(long long)threadIdx.x * nt + blockIdx.x] = c;
 }
 
 __device__ __forceinline__ bool sb_first(const unsigned long long* keys, long long i) {
@@ -1180,9 +1204,13 @@ __global__ void __launch_bounds__(kRsT) k_sb_emit(const unsigned long long* __re
                                                   long long N, const uint32_t* __restrict__ toff,
                                                   unsigned long long* __restrict__ up,
                                                   unsigned long long* __restrict__ lo,
-                                                  uint32_t* __restrict__ ucnt) {
+                                                  uint32_t* __restrict__ ucnt,
+                                                  uint32_t* __restrict__ lhist, long long nt) {
     __shared__ uint32_t cnt[kRsKpt][kRsWarps];
     __shared__ uint32_t rbase[kRsKpt];
+    __shared__ uint32_t th[2][256];  // first-pass digits of the transposes, by their tile
+    th[0][threadIdx.x] = 0;
+    th[1][threadIdx.x] = 0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const long long base = (long long)blockIdx.x * kRsTile;
@@ -1214,6 +1242,7 @@ __global__ void __launch_bounds__(kRsT) k_sb_emit(const unsigned long long* __re
     }
     __syncthreads();
     uint32_t run = toff[blockIdx.x];
+    const uint32_t t0 = run / (uint32_t)kRsTile;  // this tile's keys land in transpose tiles t0, t0 + 1
 #pragma unroll
     for (int i = 0; i < kRsKpt; i++) {
         const bool f = (firsts >> i) & 1u;
@@ -1226,23 +1255,35 @@ __global__ void __launch_bounds__(kRsT) k_sb_emit(const unsigned long long* __re
             const uint32_t p = run + before + (uint32_t)__popc(m & lt);
             up[p] = k[i];
             lo[p] = (k[i] << 32) | row;
+            atomicAdd(&th[p / (uint32_t)kRsTile - t0][(unsigned)k[i] & 255u], 1u);
         }
         const unsigned peers = __match_any_sync(kFull, f ? row : 0xffffffffu);
         if (f && (peers & lt) == 0) atomicAdd(&ucnt[row], (uint32_t)__popc(peers));
         run += rbase[i];
     }
+    __syncthreads();
+    if (th[0][threadIdx.x]) atomicAdd(&lhist[(long long)threadIdx.x * nt + t0], th[0][threadIdx.x]);
+    if (th[1][threadIdx.x]) atomicAdd(&lhist[(long long)threadIdx.x * nt + t0 + 1], th[1][threadIdx.x]);
 }
 
 // Positions [U, S) of up and lo (U = the distinct count, toff[nt]) get
 // kNoKey, so the transposed keys sort after every real one and both emits
 // skip them.
+// They count as digit 255 in the transposes' first-pass histogram.
 __global__ void k_sb_tail(const uint32_t* __restrict__ total, long long S,
-                          unsigned long long* __restrict__ up, unsigned long long* __restrict__ lo) {
+                          unsigned long long* __restrict__ up, unsigned long long* __restrict__ lo,
+                          uint32_t* __restrict__ lhist, long long nt) {
     const long long U = (long long)*total;
-    for (long long p = U + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < S;
-         p += (long long)gridDim.x * blockDim.x) {
+    const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long p = U + g0; p < S; p += gs) {
         up[p] = kNoKey;
         lo[p] = kNoKey;
+    }
+    for (long long t = U / kRsTile + g0; t < nt; t += gs) {
+        const long long a = U > t * kRsTile ? U : t * kRsTile;
+        const long long b = S < (t + 1) * kRsTile ? S : (t + 1) * kRsTile;
+        if (b > a) atomicAdd(&lhist[255LL * nt + t], (uint32_t)(b - a));
     }
 }
 
@@ -1462,10 +1503,13 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     const long long nt = (N + kRsTile - 1) / kRsTile;
     unsigned long long *keys = nullptr, *alt = nullptr, *third = nullptr, *sorted = nullptr;
     uint32_t *ucnt = nullptr, *su = nullptr, *tsum = nullptr, *toff = nullptr;
+    uint32_t *khist = nullptr, *lhist = nullptr;  // first-pass digit counts of both sorts
     KC_TRY(tmp.reserve(3 * Temp::round(8 * (size_t)N) + Temp::round(4 * nn) + Temp::round(4 * (nn + 1)) +
-                       2 * Temp::round(4 * (nt + 1)) + 2 * Temp::round(4 * 256 * (size_t)nt) +
+                       2 * Temp::round(4 * (nt + 1)) + 4 * Temp::round(4 * 256 * (size_t)nt) +
                        scan_scratch_bytes(256 * nt) + scan_scratch_bytes(nt) + 2 * scan_scratch_bytes(n)),
            "temporaries");
+    KC_TRY(tmp.get(&khist, (size_t)256 * nt), "digit counts");
+    KC_TRY(tmp.get(&lhist, (size_t)256 * nt), "digit counts");
     KC_TRY(tmp.get(&keys, (size_t)N), "keys");
     KC_TRY(tmp.get(&alt, (size_t)N), "keys");
     KC_TRY(tmp.get(&third, (size_t)N), "keys");
@@ -1475,15 +1519,17 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     KC_TRY(tmp.get(&toff, (size_t)nt + 1), "tile offsets");
     KC_TRY(cudaMemsetAsync(ucnt, 0, sizeof(uint32_t) * nn, st), "memset");
     if (S > 0) {
-        k_sb_keys<<<grid_for(S, 256), 256, 0, st>>>(src, dst, S, (int)n, keys, bc, remap);
+        k_sb_keys<<<(unsigned)nt, kRsT, 0, st>>>(src, dst, S, (int)n, keys, bc, remap, khist, nt);
         count_launch();
         KC_TRY(cudaGetLastError(), "keys");
     } else {
         KC_TRY(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long), st), "keys");
     }
     const int bits = id_bits(n);
-    // 1. the canonical keys by (a, b)
-    KC_TRY(radix_sort(KeyIn{keys}, N, alt, keys, bits, bits, st, &sorted, &tmp, (int*)nullptr), "sort");
+    // 1. the canonical keys by (a, b); the first pass's digits (byte 0) were
+    // counted with the keys
+    KC_TRY(radix_sort(KeyIn{keys}, N, alt, keys, bits, bits, st, &sorted, &tmp, (int*)nullptr,
+                      S > 0 ? khist : nullptr), "sort");
     unsigned long long* up = sorted == keys ? alt : keys;
     unsigned long long* lo = third;
     // 2. the distinct ones, with their transposes, and the upper counts
@@ -1491,16 +1537,20 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     count_launch();
     KC_TRY(cudaGetLastError(), "distinct count");
     KC_TRY(exclusive_scan(ReadU32{tsum}, nt, toff, true, st, &tmp), "tile scan");
-    k_sb_emit<<<(unsigned)nt, kRsT, 0, st>>>(sorted, N, toff, up, lo, ucnt);
+    KC_TRY(cudaMemsetAsync(lhist, 0, sizeof(uint32_t) * 256 * nt, st), "memset");
+    k_sb_emit<<<(unsigned)nt, kRsT, 0, st>>>(sorted, N, toff, up, lo, ucnt, lhist, nt);
     count_launch();
-    k_sb_tail<<<grid_for(N, 256), 256, 0, st>>>(toff + nt, N, up, lo);
+    k_sb_tail<<<grid_for(N, 256), 256, 0, st>>>(toff + nt, N, up, lo, lhist, nt);
     count_launch();
     KC_TRY(cudaGetLastError(), "emit");
     KC_TRY(exclusive_scan(ReadU32{ucnt}, n, su, true, st, &tmp), "upper offsets");
     // 3. the transposes by b (stable: a stays ascending within a row)
     unsigned long long* lsorted = nullptr;
     unsigned long long* lalt = sorted;  // free once the emit has read it
-    KC_TRY(radix_sort(KeyIn{lo}, N, lalt, lo, 0, bits, st, &lsorted, &tmp, (int*)nullptr), "transpose sort");
+    // (the first pass's digits, byte 4, were counted by the emit and the tail;
+    // with no id bits the single pass would read byte 0 instead)
+    KC_TRY(radix_sort(KeyIn{lo}, N, lalt, lo, 0, bits, st, &lsorted, &tmp, (int*)nullptr,
+                      bits > 0 ? lhist : nullptr), "transpose sort");
     kcore_status s = dmalloc(&out->row_ptr, (size_t)off_bytes * (n + 1), err, st);
     if (s != KCORE_OK) return s;
     s = dmalloc((void**)&out->col, sizeof(int) * std::max<size_t>(2 * (size_t)N, 1), err, st);
