@@ -463,17 +463,22 @@ def run_ours(args):
     src_h = torch.from_numpy(g0.src).pin_memory()
     dst_h = torch.from_numpy(g0.dst).pin_memory()
     out_h = torch.empty(g0.n, dtype=torch.int32).pin_memory()
-    e2e_t = []
+    e2e_t, e2e_create, e2e_run, e2e_call = [], [], [], []
     for i in range(args.warmup + args.steps):
         flush_l2()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gh = K.Graph.from_coo(g0.n, src_h.numpy(), dst_h.numpy(), rp_bytes, options=opts)
+        tc = time.perf_counter()
         gh.run(out=out_h.numpy())
         t1 = time.perf_counter()
+        st_h = gh.stats()
         gh.close()
         if i >= args.warmup:
             e2e_t.append(t1 - t0)
+            e2e_call.append(tc - t0)
+            e2e_create.append(st_h["ms_create"])
+            e2e_run.append(st_h["ms_run"])
     e2e_value = m * ws / statistics.mean(e2e_t)
     del src_h, dst_h, src_d, dst_d
 
@@ -501,7 +506,11 @@ def run_ours(args):
                       "options": tuned or "library defaults",
                       "autotune_s": t_tune},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * g0.samples,
-                    "d2h_bytes_per_step": 4 * g0.n},
+                    "d2h_bytes_per_step": 4 * g0.n,
+                    "ms_per_step": 1e3 * statistics.mean(e2e_t),
+                    "create_call_ms": 1e3 * statistics.mean(e2e_call),
+                    "create_events_ms": statistics.mean(e2e_create),
+                    "run_events_ms": statistics.mean(e2e_run)},
             "gpu_launches": launches,
             "create_ms": create_ms,
             "decompose": {"value": m / (statistics.mean(run_ms) / 1e3), "unit": UNIT,

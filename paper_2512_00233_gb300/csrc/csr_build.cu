@@ -1116,32 +1116,25 @@ __global__ void k_tier_out(const uint32_t* off, int nb, const void* row_ptr, int
 constexpr int kSbU = 4;
 
 // One key per sample: its canonical form (min << 32 | max) of the two
-// (renumbered) ends; a loop or a bad id becomes kNoKey.  A CTA makes one tile
-// of kRsTile keys (the radix sort's tiles) and counts their lowest bytes, the
-// digits of the sort's first pass, into column blockIdx.x of the digit-major
-// count matrix `hist`, which saves that pass its histogram read.
-__global__ void __launch_bounds__(kRsT) k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst,
-                                                  long long S, int n, unsigned long long* __restrict__ keys,
-                                                  BuildCtl* bc, const int* __restrict__ remap,
-                                                  uint32_t* __restrict__ hist, long long nt) {
-    __shared__ uint32_t sh[kRsWarps][256];
-    const int w = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < kRsWarps; q++) sh[q][threadIdx.x] = 0;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * kRsTile;
-    for (int i0 = 0; i0 < kRsKpt; i0 += kSbU) {
+// (renumbered) ends; a loop or a bad id becomes kNoKey.  (Counting the first
+// radix pass's digits here, a tile per CTA, made this kernel slower by more
+// than the histogram pass it saved.)
+__global__ void k_sb_keys(const int* __restrict__ src, const int* __restrict__ dst, long long S,
+                          int n, unsigned long long* __restrict__ keys, BuildCtl* bc,
+                          const int* __restrict__ remap) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < S; i0 += kSbU * stride) {
         int s[kSbU], d[kSbU];
         bool ok[kSbU];
 #pragma unroll
         for (int r = 0; r < kSbU; r++) {
-            const long long i = base + (long long)(i0 + r) * kRsT + threadIdx.x;
+            const long long i = i0 + r * stride;
             s[r] = i < S ? src[i] : 0;
             d[r] = i < S ? dst[i] : 0;
         }
 #pragma unroll
         for (int r = 0; r < kSbU; r++) {
-            const long long i = base + (long long)(i0 + r) * kRsT + threadIdx.x;
+            const long long i = i0 + r * stride;
             const bool in = (unsigned)s[r] < (unsigned)n && (unsigned)d[r] < (unsigned)n;
             if (i < S && !in) bc->bad = 1;
             ok[r] = i < S && in && s[r] != d[r];
@@ -1157,19 +1150,12 @@ __global__ void __launch_bounds__(kRsT) k_sb_keys(const int* __restrict__ src, c
         }
 #pragma unroll
         for (int r = 0; r < kSbU; r++) {
-            const long long i = base + (long long)(i0 + r) * kRsT + threadIdx.x;
+            const long long i = i0 + r * stride;
             if (i >= S) continue;
             const unsigned lo = (unsigned)min(s[r], d[r]), hi = (unsigned)max(s[r], d[r]);
-            const unsigned long long k = ok[r] ? ((unsigned long long)lo << 32) | hi : kNoKey;
-            keys[i] = k;
-            atomicAdd(&sh[w][(unsigned)k & 255u], 1u);
+            keys[i] = ok[r] ? ((unsigned long long)lo << 32) | hi : kNoKey;
         }
     }
-    __syncthreads();
-    uint32_t c = 0;
-#pragma unroll
-    for (int q = 0; q < kRsWarps; q++) c += sh[q][threadIdx.x];
-    hist[(long long)threadIdx.x * nt + blockIdx.x] = c;
 }
 
 __device__ __forceinline__ bool sb_first(const unsigned long long* keys, long long i) {
@@ -1503,12 +1489,11 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     const long long nt = (N + kRsTile - 1) / kRsTile;
     unsigned long long *keys = nullptr, *alt = nullptr, *third = nullptr, *sorted = nullptr;
     uint32_t *ucnt = nullptr, *su = nullptr, *tsum = nullptr, *toff = nullptr;
-    uint32_t *khist = nullptr, *lhist = nullptr;  // first-pass digit counts of both sorts
+    uint32_t* lhist = nullptr;  // first-pass digit counts of the transposes' sort
     KC_TRY(tmp.reserve(3 * Temp::round(8 * (size_t)N) + Temp::round(4 * nn) + Temp::round(4 * (nn + 1)) +
-                       2 * Temp::round(4 * (nt + 1)) + 4 * Temp::round(4 * 256 * (size_t)nt) +
+                       2 * Temp::round(4 * (nt + 1)) + 3 * Temp::round(4 * 256 * (size_t)nt) +
                        scan_scratch_bytes(256 * nt) + scan_scratch_bytes(nt) + 2 * scan_scratch_bytes(n)),
            "temporaries");
-    KC_TRY(tmp.get(&khist, (size_t)256 * nt), "digit counts");
     KC_TRY(tmp.get(&lhist, (size_t)256 * nt), "digit counts");
     KC_TRY(tmp.get(&keys, (size_t)N), "keys");
     KC_TRY(tmp.get(&alt, (size_t)N), "keys");
@@ -1519,17 +1504,15 @@ kcore_status sorted_build(Temp& tmp, int64_t n, long long S, const int* src, con
     KC_TRY(tmp.get(&toff, (size_t)nt + 1), "tile offsets");
     KC_TRY(cudaMemsetAsync(ucnt, 0, sizeof(uint32_t) * nn, st), "memset");
     if (S > 0) {
-        k_sb_keys<<<(unsigned)nt, kRsT, 0, st>>>(src, dst, S, (int)n, keys, bc, remap, khist, nt);
+        k_sb_keys<<<grid_for(S, 256), 256, 0, st>>>(src, dst, S, (int)n, keys, bc, remap);
         count_launch();
         KC_TRY(cudaGetLastError(), "keys");
     } else {
         KC_TRY(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long), st), "keys");
     }
     const int bits = id_bits(n);
-    // 1. the canonical keys by (a, b); the first pass's digits (byte 0) were
-    // counted with the keys
-    KC_TRY(radix_sort(KeyIn{keys}, N, alt, keys, bits, bits, st, &sorted, &tmp, (int*)nullptr,
-                      S > 0 ? khist : nullptr), "sort");
+    // 1. the canonical keys by (a, b)
+    KC_TRY(radix_sort(KeyIn{keys}, N, alt, keys, bits, bits, st, &sorted, &tmp, (int*)nullptr), "sort");
     unsigned long long* up = sorted == keys ? alt : keys;
     unsigned long long* lo = third;
     // 2. the distinct ones, with their transposes, and the upper counts
