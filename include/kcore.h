@@ -102,7 +102,9 @@ typedef struct kcore_options {
                                productive sweep lowers the sum of estimates)       */
     double   timeout_s;     /* budget of every bounded device wait (default 20 s)   */
     int32_t  build_sort;    /* cleaning of raw edge samples (kcore_create_coo and
-                               batches): 1 = one radix sort of all entries;
+                               batches): 1 = radix sorts of the samples'
+                               canonical (min, max) keys and of the distinct
+                               edges' transposes;
                                -1 = rows counted, filled and sorted one by one;
                                0 (default) = the sort when the input has at least
                                2^18 samples, 2*samples >= 8n, and rows of more
