@@ -223,6 +223,13 @@ def cleaner_cases():
     cases.append(("single_vertex", 1, np.zeros(3, np.int32), np.zeros(3, np.int32)))
     g = graphgen.rmat(1 << 13, 16 << 13, 0.57, 0.19, 0.19, seed=4)
     cases.append(("rmat13", g.n, g.src, g.dst))
+    # vertices but no samples at all
+    cases.append(("no_samples", 5, np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    # 200,000 samples of 500 edges: the distinct edges fill one tile of the
+    # sorted keys and the dropped repeats span dozens
+    e = rng.integers(0, 300, (500, 2)).astype(np.int32)
+    pick = rng.integers(0, 500, 200000)
+    cases.append(("heavy_repeats", 300, e[pick, 0].copy(), e[pick, 1].copy()))
     return cases
 
 
