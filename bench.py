@@ -664,6 +664,11 @@ def serve_batched(K, opts, graphs, arrivals):
     return wall, lat, res, stats, overlap
 
 
+def autotune_serve_space():
+    from paper_2512_00233_gb300 import autotune
+    return list(autotune.SERVE_SPACE)
+
+
 def run_stream(args, K, torch, after_timed=None):
     """The batching / serving workload: the first --stream-count graphs of the
     stream (n log-uniform in [100, 200000]; ER avg degree 8, R-MAT 8n samples,
@@ -760,7 +765,7 @@ def run_stream(args, K, torch, after_timed=None):
         "arena_gib": args.arena_gib, "host_staging_gib": args.host_staging_gib,
         "chunk_sweeps": opts.chunk_sweeps,
         "serve_options": serve_tuned or "library defaults",
-        "serve_tune": (f"coordinate descent over {sorted(['chunk_sweeps', 'block', 't_hi', 'med_chunk'])} "
+        "serve_tune": (f"coordinate descent over {sorted(autotune_serve_space())} "
                        f"on the first {min(G, args.serve_tune_graphs)} graphs, {t_tune:.1f} s")
         if serve_tuned else None,
         "latency": "arrival (time.perf_counter before the request is handed in) to the result "

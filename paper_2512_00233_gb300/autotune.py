@@ -13,9 +13,9 @@ n, of the average degree and of the maximum degree), so graphs of the same
 shape reuse a tuning: `tuned_options(graph)`.
 
 `autotune_serve` tunes the batch engine the same way on a sample of a graph
-stream: sweeps per persistent launch and the sweep knobs of the arena, by the
-saturated throughput (graphs/s) of the sample, every result checked against
-the first candidate's.
+stream: sweeps per persistent launch, the sweep knobs of the arena and the
+cleaner its admissions use, by the saturated throughput (graphs/s) of the
+sample, every result checked against the first candidate's.
 """
 from __future__ import annotations
 
@@ -137,6 +137,7 @@ SERVE_SPACE = {
     "block": [256, 512],
     "t_hi": [256, 1024, 2048],
     "med_chunk": [1, 4, 16],
+    "build_sort": [0, 1, -1],   # the admission's cleaner: automatic, sorted, counted
 }
 
 
