@@ -48,6 +48,27 @@ def test_batch_results_match_oracle_and_alone(staging):
     assert s["launches"] >= 1 and s["latency_p99_ms"] >= s["latency_p50_ms"] > 0
 
 
+def test_serve_autotuner_returns_a_timed_candidate_with_oracle_results():
+    """The batch engine's tuner (coordinate descent: sweeps per launch, the
+    cleaner its admissions use) times every candidate once per pass and
+    returns one of them; the engine under the result gives the oracle's
+    coreness for every graph."""
+    from paper_2512_00233_gb300 import autotune
+    graphs = stream(24, 20000, seed=11)
+    base = K.default_serve_options(mem_budget=256 << 20, chunk_sweeps=8)
+    space = {"chunk_sweeps": [4, 16], "build_sort": [1, -1]}
+    best, trials = autotune.autotune_serve(graphs, base, reps=1, space=space)
+    assert (trials[0][0], trials[0][1]) == ("base", None) and len(trials) == 5
+    assert all(rate > 0 for _, _, rate in trials)
+    assert best.chunk_sweeps in (4, 8, 16) and best.sweep.build_sort in (0, 1, -1)
+    with K.BatchEngine(best) as eng:
+        tickets = [eng.submit_coo(g.n, g.src, g.dst) for g in graphs]
+        for g, t in zip(graphs, tickets):
+            st, core = eng.poll(t, g.n, timeout_us=-1)
+            assert st == K.KCORE_OK, K.lib().kcore_last_error()
+            np.testing.assert_array_equal(core, oracle_core(g))
+
+
 def test_arrivals_while_others_run_are_admitted_and_unchanged():
     """Waves of submissions while earlier graphs are resident; one sweep per
     chunk forces admissions between the sweeps of graphs already running."""
